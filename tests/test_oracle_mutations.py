@@ -1,0 +1,76 @@
+"""The oracle pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of the oracle source (a sign, a
+weight, a coefficient, a dropped term, a boundary rule), builds it on the CPU
+and runs the pin that must fail on it.  This is what makes the pins evidence:
+a pin suite that passes on a broken oracle would prove nothing.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "eulbfs_oracle.c")
+PINS = "tests/test_oracle_pins.py::"
+
+# (name, original text, planted text, pin that must fail)
+MUTATIONS = [
+    ("f_star_sign_R3", "const double fstar = feqf + (1.0 - 1.0 / (2.0 * tau_f)) * fneqm;",
+     "const double fstar = feqf - (1.0 - 1.0 / (2.0 * tau_f)) * fneqm;", "test_simple_shear_viscous_flux"),
+    ("gamma_one_R8", "const double Gamma = CS2 * (eu / CS2", "const double Gamma = CS2 * (1.0 + eu / CS2",
+     "test_uniform_state_euler_fluxes"),
+    ("diagonal_weight", "1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};", "1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 30};",
+     "test_equilibria_moments"),
+    ("rk3_coefficient", "0.75 * s->Wn[k][c] + 0.25 * s->W[k][c]", "0.7 * s->Wn[k][c] + 0.3 * s->W[k][c]",
+     "test_rk3_mode_decay"),
+    ("phase_source_sign", "FE[4] = C * kv * D;", "FE[4] = -C * kv * D;", "test_volume_change_sources"),
+    ("pressure_source_sign", "rho * CS2 * kv * D;\n", "- rho * CS2 * kv * D;\n", "test_volume_change_sources"),
+    ("muc_sign_R5", "- s->kappa * lap;", "+ s->kappa * lap;", "test_flat_interface_equilibrium"),
+    ("surface_tension_sign", "const double Fsx = -Fl * C * s->grx[P_MUC][q];",
+     "const double Fsx = Fl * C * s->grx[P_MUC][q];", "test_three_phase_expansion_law"),
+    ("ibm_force_sign", "const double Fix = -rho * u * D, Fiy = -rho * v * D;",
+     "const double Fix = rho * u * D, Fiy = rho * v * D;", "test_freezing_momentum_decay"),
+    ("enthalpy_source_dropped", "FE[0] = Cp * T * divu;", "FE[0] = 0.0 * divu;", "test_three_phase_expansion_law"),
+    ("density_gradient_source_dropped",
+     "FE[1] = u * (s->grx[P_RHO][q] * CS2) + v * (s->gry[P_RHO][q] * CS2) +", "FE[1] = 0.0 +",
+     "test_three_phase_expansion_law"),
+    ("gravity_sign", "FE[3] = CS2 * (Fsy + rho * s->P.gy + Fiy);", "FE[3] = CS2 * (Fsy - rho * s->P.gy + Fiy);",
+     "test_hydrostatic_pressure"),
+    ("tau_h_heat_capacity", "const double tau_h = 0.5 + lamf / (rho_f * s->Cref * CS2 * dts);",
+     "const double tau_h = 0.5 + lamf / (rho_f * Cpf * CS2 * dts);", "test_pure_conduction_face_flux"),
+    ("reconstruction_offset_sign", "+ (y - (cj + 0.5)) * s->gry[f][q];", "- (y - (cj + 0.5)) * s->gry[f][q];",
+     "test_linear_temperature_convective_diffusive_flux"),
+    ("tie_rule_R7", "q[a][f] = 0.5 * (recon(s, f, Li, Lj, sx, sy) + recon(s, f, Ri, Rj, sx, sy));",
+     "q[a][f] = recon(s, f, Li, Lj, sx, sy);", "test_mirror_symmetry"),
+    ("geq_rest_coefficient", "if (a == 0) return C - muc * Qg * (1.0 - WA[0]) / CS2;",
+     "if (a == 0) return C - muc * Qg * (1.0 - WA[0]);", "test_equilibria_moments"),
+    ("heq_quadratic", "(Cref / Cp + eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));",
+     "(Cref / Cp + eu / CS2 + eu * eu / (2.0 * CS2) - uu / (2.0 * CS2));", "test_equilibria_moments"),
+    ("solid_branch_heat_capacity", "*T = H / cps;", "*T = H / cpl;", "test_enthalpy_inversion_values"),
+    ("wetting_sign_R11", "return vm + (2.0 * k - 1.0) * (4.0 * cos(th)", "return vm - (2.0 * k - 1.0) * (4.0 * cos(th)",
+     "test_contact_angle"),
+    ("dirichlet_ghost", "2.0 * sd->Tw - vm : vm;", "sd->Tw : vm;", "test_neumann_two_phase_front"),
+    ("noslip_tangential", "if (sd->flow == OR_BC_NOSLIP) return -vm;",
+     "if (sd->flow == OR_BC_NOSLIP) return f == normal_f ? -vm : vm;", "test_poiseuille_profile"),
+    ("rigid_solid_R15", "const double keep = 1.0 - clamp01(s->W[4][c]) * (1.0 - Fl);", "const double keep = 1.0;",
+     "test_rigid_solid"),
+    ("lagged_rate_R14", "s->dFs[c] = (Fs - s->Fsp[c]) / dt;", "s->dFs[c] = 0.5 * (Fs - s->Fsp[c]) / dt;",
+     "test_freezing_momentum_decay"),
+]
+
+
+@pytest.mark.parametrize("name,orig,planted,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pin_catches_planted_mistake(name, orig, planted, pin, tmp_path):
+    src = open(SRC).read()
+    assert src.count(orig) == 1, f"mutation anchor for {name} not found exactly once"
+    mut_c = tmp_path / "mut.c"
+    mut_so = tmp_path / "libmut.so"
+    mut_c.write_text(src.replace(orig, planted))
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-fPIC", "-shared", "-D_DEFAULT_SOURCE",
+                           "-I", os.path.join(ROOT, "oracle"), "-o", str(mut_so), str(mut_c), "-lm"])
+    env = dict(os.environ, EULBFS_ORACLE_LIB=str(mut_so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", PINS + pin],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pin {pin} passed on an oracle with '{name}' planted:\n{r.stdout[-2000:]}"
