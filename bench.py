@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Throughput of the EULBFS explicit step on GB300 (one JSON line on stdout).
+
+Workload: the batched static-droplet freezing problem -- 64 domains with
+sides drawn from {128, 192, 256, 384, 512} (6.76 M cells), FP32 arithmetic
+with compensated H and C, every stage of every domain in one launch over a
+tile work list.  A step is one full SSP-RK3 time step of every domain.
+Metric: GCUPS = cells x steps / s / 1e9, whole job over all ranks.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With --gpus N > 1 (launched by torchrun) every rank advances its own batch
+of 64 domains (independent problems, weak scaling, no data-path collective).
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+BYTES_PER_CELL_STEP = {1: 244, 0: 352}    # algorithmic HBM bytes per cell per time step (FP32C, FP64)
+STAGES = 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="eulbfs", choices=["eulbfs", "reference"])
+    ap.add_argument("--domains", type=int, default=64)
+    ap.add_argument("--seed", type=int, default=4)
+    ap.add_argument("--tile", type=int, default=8)
+    ap.add_argument("--graph", type=int, default=0, help="steps per captured CUDA graph (0: direct launches)")
+    ap.add_argument("--fp64-steps", type=int, default=30)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Each rank solves its own independent batch."""
+    return base + 1000 * rank
+
+
+def reduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def workload(n_domains: int, seed: int):
+    from paper_2507_03366_gb300 import workloads as wl
+    return wl.static_droplet_batch(n_domains, seed=seed)
+
+
+def cpu_baseline(cases, seconds: float) -> dict:
+    """The oracle as it stands, single-threaded, on the first domains of the
+    batch for a bounded number of steps (a partial-run rate)."""
+    import oracle
+    case = min(cases, key=lambda c: c.cells)
+    s = oracle.OracleSolver(case)
+    s.step(1)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < seconds:
+        s.step(2)
+        steps += 2
+    el = time.perf_counter() - t0
+    return {"value": case.cells * steps / el / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps of domain {case.name} ({case.nx}x{case.ny}) of the batch, "
+                      f"single-threaded FP64 oracle, {el:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    cases = workload(args.domains, rank_seed(args.seed, 0))
+    import oracle
+    case = min(cases, key=lambda c: c.cells)
+    s = oracle.OracleSolver(case)
+    for _ in range(args.warmup):
+        s.step(1)
+    # a bounded sample: at most ~2 minutes of oracle work for the whole run
+    steps = max(1, min(args.steps, int(120.0 * 1.2e5 / case.cells)))
+    t0 = time.perf_counter()
+    s.step(steps)
+    el = time.perf_counter() - t0
+    value = case.cells * steps / el / 1e9
+    line = {"impl": "reference", "metric": "GCUPS coupled EULBFS step (FP64 CPU oracle)", "value": value,
+            "unit": "GCUPS", "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"static droplet batch sample: domain {case.name} ({case.nx}x{case.ny})",
+                       "global_batch": 1, "seq_len": case.cells, "parallelism": "none (host cores)"},
+            "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{steps} steps of {case.name}"},
+            "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2507_03366_gb300 import eulbfs
+
+    cases = workload(args.domains, rank_seed(args.seed, rank))
+    cells = sum(c.cells for c in cases)
+    stream = torch.cuda.Stream()
+    sol = eulbfs.Solver(cases, precision=eulbfs.FP32C, stream=stream.cuda_stream)
+    sol.set_tile(args.tile)
+    if args.graph:
+        sol.use_graphs(args.graph)
+    for _ in range(max(3, args.warmup)):
+        sol.step(1)
+    sol.sync()
+
+    # ---- device-resident timed region ----------------------------------------
+    clocks = ClockSampler(torch.cuda.current_device())
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    sol.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    sol.sync()   # raises on a non-finite state
+    ms = ev0.elapsed_time(ev1)
+    ms_max = reduce_max(ms, world)
+    total_cells = reduce_sum(float(cells), world)
+    value = total_cells * args.steps / (ms_max * 1e-3) / 1e9
+    launches = STAGES * args.steps
+
+    # ---- roofline of the stage kernel (the only kernel in the region) --------
+    peaks = measured_peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    per_launch_ms = ms / launches
+    alg_bytes = BYTES_PER_CELL_STEP[1] / STAGES * cells
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "peak_source": "measured" if peaks else "fallback",
+                "kernel": "eulbfs::stage_kernel<float,%d>" % args.tile,
+                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": per_launch_ms}
+
+    # ---- FP64 plain GPU step on the same workload ------------------------------
+    fp64 = None
+    if args.fp64_steps > 0:
+        s64 = eulbfs.Solver(cases, precision=eulbfs.FP64, stream=stream.cuda_stream)
+        s64.set_tile(args.tile)
+        s64.step(2)
+        s64.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s64.step(args.fp64_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": cells * args.fp64_steps / (ms64 * 1e-3) / 1e9, "unit": "GCUPS",
+                "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps}
+        s64.close()
+
+    # ---- end to end through the public API with host buffers -------------------
+    e2e = None
+    if not args.no_e2e:
+        sol.close()
+        del sol
+        torch.cuda.synchronize()
+        pinned = []
+        for c in cases:   # the caller's inputs in pinned host memory
+            for k in list(c.init):
+                t = torch.empty(c.init[k].shape, dtype=torch.float64, pin_memory=True)
+                t.numpy()[...] = c.init[k]
+                pinned.append(t)
+                c.init[k] = t.numpy()
+        outs = [{k: torch.empty(c.cells, dtype=torch.float64, pin_memory=True).numpy()
+                 for k in ("H", "T", "Fl", "C", "p", "u", "v")} for c in cases]
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = eulbfs.Solver(cases, precision=eulbfs.FP32C, stream=stream.cuda_stream)
+        s2.set_tile(args.tile)
+        s2.step(args.steps)
+        for k, c in enumerate(cases):
+            fo = eulbfs.FieldsOut(*[eulbfs._ptr(outs[k][f]) for f in ("H", "T", "Fl", "C", "p", "u", "v")])
+            eulbfs._check(eulbfs.lib().eulbfs_fields(s2._h, k, fo))
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        barrier(world)
+        el = reduce_max(el, world)
+        s2.close()
+        h2d = sum(8 * c.cells * 6 for c in cases)
+        d2h = sum(8 * c.cells * 7 for c in cases)
+        e2e = {"value": total_cells * args.steps / el / 1e9, "unit": "GCUPS",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "note": "solver creation from pinned host fields, K steps, all fields back to pinned host"}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+    cpu = None if args.no_cpu else cpu_baseline(cases, args.cpu_seconds)
+    line = {
+        "metric": "GCUPS coupled EULBFS step, FP32 batched vs FP64 plain; p50/p99 solve latency",
+        "value": value, "unit": "GCUPS", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (H, C compensated hi/lo)", "data": "synthetic",
+        "config": {"workload": f"static droplet freezing batch: {len(cases)} domains per GPU, sides "
+                               f"{{128,192,256,384,512}}, {cells} cells per GPU",
+                   "global_batch": len(cases) * world, "seq_len": cells, "parallelism": f"independent domains x{world}",
+                   "precision": "FP32C", "tile": f"32x{args.tile}", "graph_steps": args.graph,
+                   "l2": "working set > L2 (state 28 B/cell read + written per stage over 6.76 M cells)"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "fp64_plain": fp64,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

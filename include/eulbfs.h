@@ -1,0 +1,215 @@
+/*
+ * eulbfs.h -- C ABI of the GB300 (sm_103a) EULBFS explicit time step.
+ *
+ * Method: Zhou, Yang, Wang, Wu, Niu, "An Enthalpy-Based Unified Lattice
+ * Boltzmann Flux Solver for Liquid Solidification", arXiv 2507.03366.
+ * One call of eulbfs_step advances every resident domain by whole time
+ * steps of Sec. 2.5: face fluxes of H, p, rho cs^2 u and C reconstructed from
+ * local D2Q9 equilibria (Eq. 54-56, 13/16, 35/37, 44/46, 53), cell sources
+ * (Eq. 51), SSP-RK3 (Eq. 58) and enthalpy inversion (Eq. 5-7).
+ *
+ * Units are lattice units: cell size 1, lattice speed 1, cs^2 = 1/3 and the
+ * streaming step dt_s = 0.5, so the surrounding points x_f - e_a dt_s of a
+ * face lie on the neighbouring cell centres and face midpoints (Sec. 2.5
+ * step (1): they must stay inside the two cells of the face).
+ * Arrays are row-major with x fastest: element (i, j) is at j*nx + i.
+ *
+ * Conventions for every call:
+ *  - The return value is an eulbfs_status; EULBFS_OK is 0.  On failure a
+ *    message is available from eulbfs_last_error() (thread-local).
+ *  - Host arrays passed in are read during the call only (copied); host
+ *    arrays passed out are owned by the caller and must hold nx*ny doubles.
+ *  - All device memory is owned by the solver and released by
+ *    eulbfs_destroy.  There is no CPU fallback: without a usable CUDA device
+ *    creation fails with EULBFS_ECUDA.
+ *  - A solver is not thread-safe; use one host thread per solver.
+ */
+#ifndef EULBFS_H
+#define EULBFS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EULBFS_OK = 0,
+    EULBFS_EINVAL = 1,     /* invalid argument or physically invalid parameters */
+    EULBFS_ENOMEM = 2,     /* device or host allocation failed */
+    EULBFS_ECUDA = 3,      /* CUDA runtime error (no device, launch failure, ...) */
+    EULBFS_ENONFINITE = 4, /* the state of some domain became NaN or Inf */
+    EULBFS_ETIMEOUT = 5,   /* a bounded device wait gave up (reserved) */
+    EULBFS_EBUSY = 6       /* a domain does not fit in the solver's memory budget */
+} eulbfs_status;
+
+typedef enum {
+    EULBFS_FP64 = 0,  /* all state and arithmetic in FP64 */
+    EULBFS_FP32C = 1  /* FP32 arithmetic; H and C carried as compensated hi/lo FP32 pairs */
+} eulbfs_precision;
+
+/* Boundary-condition kinds, per field family and side (Sec. 3.1-3.5).
+ * A side is periodic only if all three kinds are EULBFS_BC_PERIODIC, and then
+ * so is the opposite side. */
+typedef enum {
+    EULBFS_BC_PERIODIC = 0,
+    EULBFS_BC_DIRICHLET_T = 1, /* thermal: T = Tw on the wall face */
+    EULBFS_BC_ADIABATIC = 2,   /* thermal: zero normal gradient */
+    EULBFS_BC_NOSLIP = 3,      /* flow: u = 0 on the wall face */
+    EULBFS_BC_SYMMETRY = 4,    /* flow: zero normal velocity, free slip */
+    EULBFS_BC_OUTLET = 5,      /* flow: p = 0 on the face, zero gradient of u */
+    EULBFS_BC_NOFLUX = 6,      /* phase field: zero normal gradient of C and mu_c */
+    EULBFS_BC_WETTING = 7      /* phase field: contact angle theta_deg */
+} eulbfs_bc_kind;
+
+typedef struct { int nx, ny; } eulbfs_grid;   /* cells; nx, ny >= 2 on walled axes */
+
+/* Properties of one phase: density, dynamic viscosity, thermal conductivity,
+ * specific heat (all > 0 except mu >= 0). */
+typedef struct { double rho, mu, lambda, cp; } eulbfs_phase;
+
+typedef struct {
+    eulbfs_phase s, l, g;  /* solid, liquid, gas; mixed by Eq. 7 */
+    double L;              /* latent heat (Eq. 5-6), >= 0 */
+    double Ts, Tl;         /* solidus <= liquidus temperature */
+    double sigma, xi;      /* interfacial tension, interface thickness (Sec. 2.3.1) */
+    double Mc;             /* mobility M_c = (tau_g - 0.5) Q_g dt_s (Sec. 2.3.2) */
+    double tau_g;          /* phase-field relaxation parameter, > 0.5 */
+    double gx, gy;         /* gravitational acceleration, G = rho g (Eq. 51) */
+    int zero_solid_velocity; /* 1: momentum of the solid part projected to zero */
+} eulbfs_props;
+
+typedef struct { int thermal, flow, phase; double Tw, theta_deg; } eulbfs_side;
+typedef struct { eulbfs_side xlo, xhi, ylo, yhi; } eulbfs_bc;
+
+typedef struct {
+    double dt;  /* Runge-Kutta time step Delta t (Eq. 58), chosen by the caller's CFL bound */
+} eulbfs_numerics;
+
+/* Initial primitive fields: host arrays of nx*ny doubles, copied at creation.
+ * T and C are required; Fl (initial liquid fraction, used only where
+ * Ts <= T <= Tl), u, v, p may be NULL (1, 0, 0, 0). */
+typedef struct { const double *T, *Fl, *C, *u, *v, *p; } eulbfs_init;
+
+/* One domain of a batch. */
+typedef struct {
+    eulbfs_grid grid;
+    eulbfs_props props;
+    eulbfs_bc bc;
+    eulbfs_numerics num;
+    eulbfs_init init;
+} eulbfs_domain;
+
+/* Host output of eulbfs_fields; any pointer may be NULL (skipped). */
+typedef struct { double *H, *T, *Fl, *C, *p, *u, *v; } eulbfs_fields_out;
+
+/* Global diagnostics of one domain, accumulated in FP64 on the device
+ * (fixed-order reduction, bitwise reproducible). */
+typedef struct {
+    long long step;       /* completed time steps */
+    double t;             /* simulated time = step * dt */
+    double mass;          /* sum of rho (cell volume 1) */
+    double enthalpy;      /* sum of H */
+    double phase_vol;     /* sum of C */
+    double solid_vol;     /* sum of clamp(C,0,1) * F_s */
+    double front_pos;     /* solid_vol / ny: solid thickness per unit width */
+    double interface_pos; /* phase_vol / ny: condensed thickness per unit width */
+    double max_speed;     /* max |u| */
+    int nonfinite;        /* 1 if any state value is NaN or Inf */
+} eulbfs_diag;
+
+typedef struct eulbfs_solver eulbfs_solver;
+
+/* Create a solver holding one domain.  stream is a cudaStream_t the solver
+ * enqueues all its work on, or NULL for a stream the solver owns.
+ * Errors: EINVAL (bad sizes or parameters: tau <= 0.5, rho/lambda/cp <= 0,
+ * inconsistent periodic sides, dt <= 0), ECUDA, ENOMEM. */
+int eulbfs_create(const eulbfs_grid* grid, const eulbfs_props* props, const eulbfs_bc* bc,
+                  const eulbfs_numerics* num, const eulbfs_init* init, int precision,
+                  void* stream, eulbfs_solver** out);
+
+/* Create a solver holding n >= 1 domains of any sizes and parameters that
+ * advance together: every stage of every domain runs in one launch over a
+ * tile work list (configs with many uneven domains). */
+int eulbfs_batch_create(int n, const eulbfs_domain* domains, int precision, void* stream,
+                        eulbfs_solver** out);
+
+/* Limit the device memory the solver may hold (bytes, 0 = unlimited).
+ * eulbfs_add_domain fails with EBUSY instead of exceeding it. */
+int eulbfs_set_memory_budget(eulbfs_solver* s, unsigned long long bytes);
+
+/* Bytes of device memory a domain of this size needs in this precision. */
+unsigned long long eulbfs_domain_bytes(int nx, int ny, int precision);
+
+/* Add a domain to a live solver (continuous batching).  max_steps > 0 stops
+ * the domain after that many steps; 0 = no limit.  *slot receives its index.
+ * Errors: EINVAL, EBUSY (memory budget), ENOMEM, ECUDA. */
+int eulbfs_add_domain(eulbfs_solver* s, const eulbfs_domain* d, long long max_steps, int* slot);
+
+/* Remove a domain and release its memory; its slot index is not reused. */
+int eulbfs_remove_domain(eulbfs_solver* s, int slot);
+
+/* Number of slots ever created (removed slots included). */
+int eulbfs_num_slots(const eulbfs_solver* s);
+
+/* Steps completed and steps left (-1 = unlimited) of a domain. */
+int eulbfs_domain_progress(const eulbfs_solver* s, int slot, long long* done, long long* left);
+
+/* Advance every active domain by n >= 0 time steps (a domain with a step
+ * limit stops at it).  Work is enqueued on the solver's stream and the call
+ * returns without waiting; launch errors are reported, a non-finite state is
+ * reported by eulbfs_sync / eulbfs_diagnostics / eulbfs_fields. */
+int eulbfs_step(eulbfs_solver* s, long long n);
+
+/* Wait for the solver's stream.  Returns ENONFINITE if a stage of any
+ * domain produced a NaN or Inf since the solver was created. */
+int eulbfs_sync(eulbfs_solver* s);
+
+/* Copy primitive fields of domain `slot` to caller-owned host arrays
+ * (synchronises the solver's stream). */
+int eulbfs_fields(eulbfs_solver* s, int slot, const eulbfs_fields_out* out);
+
+/* Conserved state W = (H, p, rho cs^2 u, rho cs^2 v, C) (Eq. 49), the
+ * previous-step solid fraction F_s^{n-1}, time and step, as doubles.  Exact in
+ * FP64; in FP32C H and C are the hi + lo pairs rounded to double (a pair can
+ * carry more than 53 significant bits), so a round trip perturbs them by at
+ * most 2^-53 relative.  Any pointer may be NULL.  set_state sets the step
+ * counter to `step` (t is recomputed as step * dt). */
+int eulbfs_get_state(eulbfs_solver* s, int slot, double* H, double* p, double* mx, double* my,
+                     double* C, double* Fs_prev, double* t, long long* step);
+int eulbfs_set_state(eulbfs_solver* s, int slot, const double* H, const double* p,
+                     const double* mx, const double* my, const double* C,
+                     const double* Fs_prev, double t, long long step);
+
+/* Bytes of a domain's raw checkpoint: its state planes and F_s^{n-1} in the
+ * solver's working precision. */
+unsigned long long eulbfs_checkpoint_bytes(const eulbfs_solver* s, int slot);
+/* Bitwise-exact checkpoint of domain `slot` into / from a caller-owned host
+ * buffer of eulbfs_checkpoint_bytes bytes (same precision and grid size on
+ * load; EINVAL otherwise).  *step receives / step sets the step counter. */
+int eulbfs_save(eulbfs_solver* s, int slot, void* buf, unsigned long long bytes, long long* step);
+int eulbfs_load(eulbfs_solver* s, int slot, const void* buf, unsigned long long bytes, long long step);
+
+/* FP64 diagnostics of domain `slot` (synchronises the solver's stream). */
+int eulbfs_diagnostics(eulbfs_solver* s, int slot, eulbfs_diag* d);
+
+/* Number of kernels the solver launches per time step of the current batch. */
+int eulbfs_launches_per_step(const eulbfs_solver* s);
+
+/* Capture eulbfs_step's per-step launches in a CUDA graph of `steps_per_graph`
+ * steps (0 disables); replays are used when n is a multiple of it. */
+int eulbfs_use_graphs(eulbfs_solver* s, int steps_per_graph);
+
+/* Tile shape (cells) of the stage kernel; 0 = the default. */
+int eulbfs_set_tile(eulbfs_solver* s, int tile_y);
+
+void eulbfs_destroy(eulbfs_solver* s);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* eulbfs_last_error(void);
+
+/* Library version string. */
+const char* eulbfs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

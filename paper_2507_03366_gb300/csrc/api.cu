@@ -1,0 +1,663 @@
+// api.cu -- host side of libeulbfs: the C ABI of include/eulbfs.h.
+//
+// A solver holds a set of domains ("slots").  Each domain owns one device
+// allocation: its descriptor, three state buffers (W^n and the two
+// intermediate Runge-Kutta stages), F_s of the previous step and the lagged
+// dF_s/dt.  The active domains form one tile work list; a time step is three
+// launches of the stage kernel over that list (Eq. 58), optionally replayed
+// from a captured CUDA graph.  Domains can be added and removed between steps
+// (continuous batching) under a device-memory budget.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "eulbfs.h"
+#include "eulbfs_internal.h"
+
+using namespace eulbfs;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(EULBFS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                    \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+constexpr double kDtStream = 0.5;   // c dt_s = dx / 2 (Sec. 2.5 step (1))
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+int planes_of(int precision) { return precision == EULBFS_FP64 ? 5 : 7; }
+size_t elem_of(int precision) { return precision == EULBFS_FP64 ? 8 : 4; }
+
+struct Dom {
+    eulbfs_grid grid{};
+    eulbfs_props props{};
+    eulbfs_bc bc{};
+    eulbfs_numerics num{};
+    DomainDesc desc{};     // host copy (device pointers filled in)
+    DomainDesc* d_desc = nullptr;  // device copy at the start of `mem`
+    void* mem = nullptr;
+    size_t bytes = 0;
+    long long done = 0;
+    long long max_steps = 0;
+    bool alive = false;    // allocated and not removed
+    bool finished() const { return max_steps > 0 && done >= max_steps; }
+    bool active() const { return alive && !finished(); }
+};
+
+bool valid_kind_side(const eulbfs_side& s, bool periodic) {
+    if (periodic)
+        return s.thermal == EULBFS_BC_PERIODIC && s.flow == EULBFS_BC_PERIODIC && s.phase == EULBFS_BC_PERIODIC;
+    return (s.thermal == EULBFS_BC_DIRICHLET_T || s.thermal == EULBFS_BC_ADIABATIC) &&
+           (s.flow == EULBFS_BC_NOSLIP || s.flow == EULBFS_BC_SYMMETRY || s.flow == EULBFS_BC_OUTLET) &&
+           (s.phase == EULBFS_BC_NOFLUX || s.phase == EULBFS_BC_WETTING);
+}
+
+int validate(const eulbfs_grid& g, const eulbfs_props& P, const eulbfs_bc& B, const eulbfs_numerics& N) {
+    if (g.nx < 1 || g.ny < 1) return fail(EULBFS_EINVAL, "nx and ny must be >= 1");
+    if ((long long)g.nx * g.ny > (1LL << 31)) return fail(EULBFS_EINVAL, "domain too large");
+    const bool px = B.xlo.thermal == EULBFS_BC_PERIODIC, py = B.ylo.thermal == EULBFS_BC_PERIODIC;
+    if (!valid_kind_side(B.xlo, px) || !valid_kind_side(B.xhi, px) || !valid_kind_side(B.ylo, py) ||
+        !valid_kind_side(B.yhi, py))
+        return fail(EULBFS_EINVAL, "inconsistent boundary conditions (a periodic side needs a periodic partner)");
+    if ((!px && g.nx < 2) || (!py && g.ny < 2)) return fail(EULBFS_EINVAL, "a walled axis needs at least 2 cells");
+    const eulbfs_phase* ph[3] = {&P.s, &P.l, &P.g};
+    for (auto* q : ph)
+        if (!(q->rho > 0 && q->cp > 0 && q->lambda > 0 && q->mu >= 0 && std::isfinite(q->rho) &&
+              std::isfinite(q->cp) && std::isfinite(q->lambda) && std::isfinite(q->mu)))
+            return fail(EULBFS_EINVAL, "phase properties must be finite, rho, lambda, cp > 0 and mu >= 0");
+    if (!(P.L >= 0 && P.Ts <= P.Tl && P.sigma >= 0 && P.Mc >= 0 && P.tau_g > 0.5))
+        return fail(EULBFS_EINVAL, "need L >= 0, Ts <= Tl, sigma >= 0, Mc >= 0, tau_g > 0.5");
+    if (P.sigma > 0 && !(P.xi > 0)) return fail(EULBFS_EINVAL, "xi must be > 0 when sigma > 0");
+    if (!(N.dt > 0 && std::isfinite(N.dt))) return fail(EULBFS_EINVAL, "dt must be > 0");
+    return EULBFS_OK;
+}
+
+DomainDesc make_desc(const eulbfs_grid& g, const eulbfs_props& P, const eulbfs_bc& B, const eulbfs_numerics& N) {
+    DomainDesc d{};
+    d.nx = g.nx;
+    d.ny = g.ny;
+    d.per_x = B.xlo.thermal == EULBFS_BC_PERIODIC;
+    d.per_y = B.ylo.thermal == EULBFS_BC_PERIODIC;
+    const eulbfs_side* sides[4] = {&B.xlo, &B.xhi, &B.ylo, &B.yhi};
+    for (int k = 0; k < 4; ++k) {
+        d.bc_t[k] = sides[k]->thermal;
+        d.bc_f[k] = sides[k]->flow;
+        d.bc_c[k] = sides[k]->phase;
+        d.Tw[k] = sides[k]->Tw;
+        d.wet[k] = (P.xi > 0) ? 4.0 * std::cos(sides[k]->theta_deg * M_PI / 180.0) / P.xi : 0.0;
+    }
+    d.zero_solid_velocity = P.zero_solid_velocity ? 1 : 0;
+    const eulbfs_phase* ph[3] = {&P.s, &P.l, &P.g};
+    for (int k = 0; k < 3; ++k) {
+        d.rho[k] = ph[k]->rho;
+        d.mu[k] = ph[k]->mu;
+        d.lam[k] = ph[k]->lambda;
+        d.cp[k] = ph[k]->cp;
+    }
+    d.L = P.L;
+    d.Ts = P.Ts;
+    d.Tl = P.Tl;
+    d.beta = P.sigma > 0 ? 12.0 * P.sigma / P.xi : 0.0;   // Sec. 2.3.1
+    d.kappa = 1.5 * P.xi * P.sigma;
+    d.tau_g = P.tau_g;
+    d.Qg = P.Mc / ((P.tau_g - 0.5) * kDtStream);         // M_c = (tau_g - 0.5) Q_g dt_s
+    d.Cref = 0.5 * (P.s.cp + P.l.cp);                    // Sec. 2.1.2
+    d.kv = 1.0 - P.s.rho / P.l.rho;
+    d.gx = P.gx;
+    d.gy = P.gy;
+    d.dt = N.dt;
+    d.plane = (long long)g.nx * g.ny;
+    return d;
+}
+
+size_t domain_bytes(long long n, int precision) {
+    const size_t e = elem_of(precision);
+    return align256(sizeof(DomainDesc)) + 3 * align256((size_t)planes_of(precision) * n * e) + 2 * align256(n * e);
+}
+
+}  // namespace
+
+struct eulbfs_solver {
+    int precision = EULBFS_FP32C;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<Dom> doms;
+    DomainDesc* d_descs = nullptr;
+    int descs_cap = 0;
+    int* d_tiles = nullptr;
+    int tiles_cap = 0;
+    int ntiles = 0;
+    bool dirty = true;
+    int tile_y = 8;
+    int sms = 1;
+    int grid = 1;
+    int* d_flag = nullptr;
+    int* h_flag = nullptr;
+    double* d_partial = nullptr;
+    int partial_cap = 0;
+    double* d_diag = nullptr;
+    double* h_diag = nullptr;
+    unsigned long long budget = 0;
+    unsigned long long used = 0;
+    int graph_steps = 0;
+    cudaGraphExec_t graph = nullptr;
+    bool graph_valid = false;
+};
+
+namespace {
+
+void drop_graph(eulbfs_solver* s) {
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+    s->graph_valid = false;
+}
+
+int rebuild(eulbfs_solver* s) {
+    const int nd = (int)s->doms.size();
+    if (nd > s->descs_cap) {
+        if (s->d_descs) cudaFree(s->d_descs);
+        s->descs_cap = std::max(nd, 2 * s->descs_cap);
+        CK(cudaMalloc(&s->d_descs, sizeof(DomainDesc) * s->descs_cap), "descriptor array");
+    }
+    std::vector<int> tiles;
+    std::vector<DomainDesc> descs(nd);
+    for (int k = 0; k < nd; ++k) {
+        Dom& d = s->doms[k];
+        d.desc.tiles_x = (d.grid.nx + kTileX - 1) / kTileX;
+        d.desc.tiles_y = (d.grid.ny + s->tile_y - 1) / s->tile_y;
+        d.desc.tile0 = (int)tiles.size();
+        if (d.active()) tiles.insert(tiles.end(), (size_t)d.desc.tiles_x * d.desc.tiles_y, k);
+        descs[k] = d.desc;
+    }
+    if (nd) CK(cudaMemcpyAsync(s->d_descs, descs.data(), sizeof(DomainDesc) * nd, cudaMemcpyHostToDevice, s->stream), "upload descriptors");
+    s->ntiles = (int)tiles.size();
+    if (s->ntiles > s->tiles_cap) {
+        if (s->d_tiles) cudaFree(s->d_tiles);
+        s->tiles_cap = std::max(s->ntiles, 2 * s->tiles_cap);
+        CK(cudaMalloc(&s->d_tiles, sizeof(int) * s->tiles_cap), "tile list");
+    }
+    if (s->ntiles) CK(cudaMemcpyAsync(s->d_tiles, tiles.data(), sizeof(int) * s->ntiles, cudaMemcpyHostToDevice, s->stream), "upload tiles");
+    // the host vectors die here: make the copies complete before returning
+    CK(cudaStreamSynchronize(s->stream), "rebuild sync");
+    const int per_sm = stage_blocks_per_sm(s->precision, s->tile_y);
+    s->grid = std::max(1, std::min(s->ntiles, per_sm * s->sms));
+    drop_graph(s);
+    s->dirty = false;
+    return EULBFS_OK;
+}
+
+int launch_step_direct(eulbfs_solver* s) {
+    StageLaunch a;
+    a.descs = s->d_descs;
+    a.tile_domain = s->d_tiles;
+    a.ntiles = s->ntiles;
+    a.flag = s->d_flag;
+    for (int st = 0; st < 3; ++st) {
+        a.stage = st;
+        cudaError_t e = launch_stage(s->precision, s->tile_y, a, s->grid, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
+    }
+    return EULBFS_OK;
+}
+
+int capture_graph(eulbfs_solver* s) {
+    drop_graph(s);
+    if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return EULBFS_ECUDA;
+    }
+    int rc = EULBFS_OK;
+    for (int k = 0; k < s->graph_steps && rc == EULBFS_OK; ++k) rc = launch_step_direct(s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    if (rc != EULBFS_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return EULBFS_ECUDA;
+    }
+    e = cudaGraphInstantiate(&s->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        s->graph = nullptr;
+        cudaGetLastError();
+        return EULBFS_ECUDA;
+    }
+    s->graph_valid = true;
+    return EULBFS_OK;
+}
+
+int check_slot(const eulbfs_solver* s, int slot) {
+    if (!s) return fail(EULBFS_EINVAL, "null solver");
+    if (slot < 0 || slot >= (int)s->doms.size() || !s->doms[slot].alive)
+        return fail(EULBFS_EINVAL, "no such domain slot");
+    return EULBFS_OK;
+}
+
+int add_domain(eulbfs_solver* s, const eulbfs_domain& dm, long long max_steps, int* slot) {
+    int rc = validate(dm.grid, dm.props, dm.bc, dm.num);
+    if (rc) return rc;
+    if (!dm.init.T || !dm.init.C) return fail(EULBFS_EINVAL, "initial T and C are required");
+    if (max_steps < 0) return fail(EULBFS_EINVAL, "max_steps must be >= 0");
+    const long long n = (long long)dm.grid.nx * dm.grid.ny;
+    const size_t bytes = domain_bytes(n, s->precision);
+    if (s->budget && s->used + bytes > s->budget)
+        return fail(EULBFS_EBUSY, "domain does not fit in the memory budget");
+    Dom d;
+    d.grid = dm.grid;
+    d.props = dm.props;
+    d.bc = dm.bc;
+    d.num = dm.num;
+    d.max_steps = max_steps;
+    d.desc = make_desc(dm.grid, dm.props, dm.bc, dm.num);
+    if (cudaMalloc(&d.mem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(EULBFS_ENOMEM, "device allocation of a domain failed");
+    }
+    d.bytes = bytes;
+    char* p = static_cast<char*>(d.mem);
+    d.d_desc = reinterpret_cast<DomainDesc*>(p);
+    p += align256(sizeof(DomainDesc));
+    const size_t e = elem_of(s->precision);
+    for (int k = 0; k < 3; ++k) {
+        d.desc.st[k] = p;
+        p += align256((size_t)planes_of(s->precision) * n * e);
+    }
+    d.desc.Fsp = p;
+    p += align256(n * e);
+    d.desc.dFs = p;
+    CK(cudaMemsetAsync(d.mem, 0, bytes, s->stream), "clear domain");
+    CK(cudaMemcpyAsync(d.d_desc, &d.desc, sizeof(DomainDesc), cudaMemcpyHostToDevice, s->stream), "upload descriptor");
+    // initial fields: H from (T, F_l, C), m = rho cs^2 u, F_s^{-1} = F_s^0
+    double* buf = nullptr;
+    if (cudaMalloc(&buf, sizeof(double) * n * 6 + 256) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d.mem);
+        return fail(EULBFS_ENOMEM, "init scratch allocation failed");
+    }
+    int* d_bad = reinterpret_cast<int*>(buf + 6 * n);
+    const double* src[6] = {dm.init.T, dm.init.Fl, dm.init.C, dm.init.u, dm.init.v, dm.init.p};
+    double* dst[6];
+    cudaError_t ce = cudaMemsetAsync(d_bad, 0, sizeof(int), s->stream);
+    for (int k = 0; k < 6; ++k) {
+        dst[k] = src[k] ? buf + k * n : nullptr;
+        if (src[k] && ce == cudaSuccess)
+            ce = cudaMemcpyAsync(dst[k], src[k], sizeof(double) * n, cudaMemcpyHostToDevice, s->stream);
+    }
+    if (ce == cudaSuccess) ce = launch_init(s->precision, d.d_desc, dst[0], dst[1], dst[2], dst[3], dst[4], dst[5], n, d_bad, s->stream);
+    int bad = 0;
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->h_flag, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+    if (ce == cudaSuccess) bad = *s->h_flag;
+    cudaFree(buf);
+    if (ce != cudaSuccess) {
+        cudaFree(d.mem);
+        return cuda_fail(ce, "domain initialisation");
+    }
+    if (bad) {
+        cudaFree(d.mem);
+        return fail(EULBFS_EINVAL, "initial fields contain NaN or Inf");
+    }
+    d.alive = true;
+    s->used += bytes;
+    s->doms.push_back(d);
+    if (slot) *slot = (int)s->doms.size() - 1;
+    s->dirty = true;
+    return EULBFS_OK;
+}
+
+int new_solver(int precision, void* stream, eulbfs_solver** out) {
+    if (!out) return fail(EULBFS_EINVAL, "out is null");
+    *out = nullptr;
+    if (precision != EULBFS_FP64 && precision != EULBFS_FP32C) return fail(EULBFS_EINVAL, "unknown precision");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(EULBFS_ECUDA, "no CUDA device available (there is no CPU fallback)");
+    }
+    eulbfs_solver* s = new eulbfs_solver();
+    s->precision = precision;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (stream) {
+        s->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete s;
+            return fail(EULBFS_ECUDA, "stream creation failed");
+        }
+        s->own_stream = true;
+    }
+    if (cudaMalloc(&s->d_flag, sizeof(int)) != cudaSuccess || cudaMallocHost(&s->h_flag, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&s->d_diag, sizeof(double) * kDiagFields) != cudaSuccess ||
+        cudaMallocHost(&s->h_diag, sizeof(double) * kDiagFields) != cudaSuccess) {
+        eulbfs_destroy(s);
+        return fail(EULBFS_ENOMEM, "solver allocation failed");
+    }
+    cudaMemsetAsync(s->d_flag, 0, sizeof(int), s->stream);
+    *out = s;
+    return EULBFS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* eulbfs_last_error(void) { return g_err.c_str(); }
+
+const char* eulbfs_version(void) { return "eulbfs-gb300 0.1 (sm_103a)"; }
+
+unsigned long long eulbfs_domain_bytes(int nx, int ny, int precision) {
+    if (nx < 1 || ny < 1) return 0;
+    return (unsigned long long)domain_bytes((long long)nx * ny, precision);
+}
+
+int eulbfs_create(const eulbfs_grid* grid, const eulbfs_props* props, const eulbfs_bc* bc,
+                  const eulbfs_numerics* num, const eulbfs_init* init, int precision, void* stream,
+                  eulbfs_solver** out) {
+    if (!grid || !props || !bc || !num || !init) return fail(EULBFS_EINVAL, "null argument");
+    eulbfs_domain d;
+    d.grid = *grid;
+    d.props = *props;
+    d.bc = *bc;
+    d.num = *num;
+    d.init = *init;
+    return eulbfs_batch_create(1, &d, precision, stream, out);
+}
+
+int eulbfs_batch_create(int n, const eulbfs_domain* domains, int precision, void* stream, eulbfs_solver** out) {
+    if (n < 1 || !domains) return fail(EULBFS_EINVAL, "need at least one domain");
+    if (!out) return fail(EULBFS_EINVAL, "out is null");
+    for (int k = 0; k < n; ++k) {
+        int rc = validate(domains[k].grid, domains[k].props, domains[k].bc, domains[k].num);
+        if (rc) return fail(rc, "domain " + std::to_string(k) + ": " + g_err);
+    }
+    eulbfs_solver* s = nullptr;
+    int rc = new_solver(precision, stream, &s);
+    if (rc) return rc;
+    for (int k = 0; k < n; ++k) {
+        rc = add_domain(s, domains[k], 0, nullptr);
+        if (rc) {
+            std::string m = g_err;
+            eulbfs_destroy(s);
+            return fail(rc, "domain " + std::to_string(k) + ": " + m);
+        }
+    }
+    *out = s;
+    return EULBFS_OK;
+}
+
+int eulbfs_set_memory_budget(eulbfs_solver* s, unsigned long long bytes) {
+    if (!s) return fail(EULBFS_EINVAL, "null solver");
+    s->budget = bytes;
+    return EULBFS_OK;
+}
+
+int eulbfs_add_domain(eulbfs_solver* s, const eulbfs_domain* d, long long max_steps, int* slot) {
+    if (!s || !d) return fail(EULBFS_EINVAL, "null argument");
+    return add_domain(s, *d, max_steps, slot);
+}
+
+int eulbfs_remove_domain(eulbfs_solver* s, int slot) {
+    int rc = check_slot(s, slot);
+    if (rc) return rc;
+    Dom& d = s->doms[slot];
+    CK(cudaStreamSynchronize(s->stream), "sync before remove");
+    cudaFree(d.mem);
+    d.mem = nullptr;
+    d.alive = false;
+    s->used -= d.bytes;
+    s->dirty = true;
+    return EULBFS_OK;
+}
+
+int eulbfs_num_slots(const eulbfs_solver* s) { return s ? (int)s->doms.size() : 0; }
+
+int eulbfs_domain_progress(const eulbfs_solver* s, int slot, long long* done, long long* left) {
+    int rc = check_slot(s, slot);
+    if (rc) return rc;
+    const Dom& d = s->doms[slot];
+    if (done) *done = d.done;
+    if (left) *left = d.max_steps > 0 ? std::max(0LL, d.max_steps - d.done) : -1;
+    return EULBFS_OK;
+}
+
+int eulbfs_set_tile(eulbfs_solver* s, int tile_y) {
+    if (!s) return fail(EULBFS_EINVAL, "null solver");
+    if (tile_y == 0) tile_y = 8;
+    if (tile_y != 4 && tile_y != 8 && tile_y != 16) return fail(EULBFS_EINVAL, "tile_y must be 4, 8 or 16");
+    if (tile_y != s->tile_y) {
+        s->tile_y = tile_y;
+        s->dirty = true;
+    }
+    return EULBFS_OK;
+}
+
+int eulbfs_use_graphs(eulbfs_solver* s, int steps_per_graph) {
+    if (!s) return fail(EULBFS_EINVAL, "null solver");
+    if (steps_per_graph < 0) return fail(EULBFS_EINVAL, "steps_per_graph must be >= 0");
+    s->graph_steps = steps_per_graph;
+    drop_graph(s);
+    return EULBFS_OK;
+}
+
+int eulbfs_launches_per_step(const eulbfs_solver* s) { return s ? 3 : 0; }
+
+int eulbfs_step(eulbfs_solver* s, long long n) {
+    if (!s) return fail(EULBFS_EINVAL, "null solver");
+    if (n < 0) return fail(EULBFS_EINVAL, "n must be >= 0");
+    while (n > 0) {
+        if (s->dirty) {
+            int rc = rebuild(s);
+            if (rc) return rc;
+        }
+        if (s->ntiles == 0) break;
+        long long k = n;
+        for (const Dom& d : s->doms)
+            if (d.active() && d.max_steps > 0) k = std::min(k, d.max_steps - d.done);
+        long long left = k;
+        if (s->graph_steps > 0) {
+            if (!s->graph_valid && left >= s->graph_steps) capture_graph(s);
+            while (s->graph_valid && left >= s->graph_steps) {
+                CK(cudaGraphLaunch(s->graph, s->stream), "graph launch");
+                left -= s->graph_steps;
+            }
+        }
+        for (; left > 0; --left) {
+            int rc = launch_step_direct(s);
+            if (rc) return rc;
+        }
+        for (Dom& d : s->doms)
+            if (d.active()) {
+                d.done += k;
+                if (d.finished()) s->dirty = true;
+            }
+        n -= k;
+    }
+    return EULBFS_OK;
+}
+
+int eulbfs_sync(eulbfs_solver* s) {
+    if (!s) return fail(EULBFS_EINVAL, "null solver");
+    CK(cudaMemcpyAsync(s->h_flag, s->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "flag copy");
+    CK(cudaStreamSynchronize(s->stream), "stream sync");
+    if (*s->h_flag & 1) return fail(EULBFS_ENONFINITE, "a non-finite state value was produced");
+    return EULBFS_OK;
+}
+
+int eulbfs_fields(eulbfs_solver* s, int slot, const eulbfs_fields_out* out) {
+    int rc = check_slot(s, slot);
+    if (rc) return rc;
+    if (!out) return fail(EULBFS_EINVAL, "null output");
+    const Dom& d = s->doms[slot];
+    const long long n = d.desc.plane;
+    double* host[7] = {out->H, out->T, out->Fl, out->C, out->p, out->u, out->v};
+    double* buf = nullptr;
+    CK(cudaMalloc(&buf, sizeof(double) * n * 7), "fields scratch");
+    double* dev[7];
+    for (int k = 0; k < 7; ++k) dev[k] = host[k] ? buf + k * n : nullptr;
+    cudaError_t e = launch_fields(s->precision, d.d_desc, n, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5], dev[6], s->stream);
+    for (int k = 0; k < 7 && e == cudaSuccess; ++k)
+        if (host[k]) e = cudaMemcpyAsync(host[k], dev[k], sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(e, "fields");
+    return eulbfs_sync(s) == EULBFS_ENONFINITE ? EULBFS_ENONFINITE : EULBFS_OK;
+}
+
+int eulbfs_get_state(eulbfs_solver* s, int slot, double* H, double* p, double* mx, double* my, double* C,
+                     double* Fs_prev, double* t, long long* step) {
+    int rc = check_slot(s, slot);
+    if (rc) return rc;
+    const Dom& d = s->doms[slot];
+    const long long n = d.desc.plane;
+    double* host[6] = {H, p, mx, my, C, Fs_prev};
+    double* buf = nullptr;
+    CK(cudaMalloc(&buf, sizeof(double) * n * 6), "state scratch");
+    double* dev[6];
+    for (int k = 0; k < 6; ++k) dev[k] = host[k] ? buf + k * n : nullptr;
+    cudaError_t e = launch_get_state(s->precision, d.d_desc, n, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5], s->stream);
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+        if (host[k]) e = cudaMemcpyAsync(host[k], dev[k], sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(e, "get_state");
+    if (t) *t = d.done * d.num.dt;
+    if (step) *step = d.done;
+    return EULBFS_OK;
+}
+
+int eulbfs_set_state(eulbfs_solver* s, int slot, const double* H, const double* p, const double* mx,
+                     const double* my, const double* C, const double* Fs_prev, double t, long long step) {
+    int rc = check_slot(s, slot);
+    if (rc) return rc;
+    (void)t;
+    if (step < 0) return fail(EULBFS_EINVAL, "step must be >= 0");
+    Dom& d = s->doms[slot];
+    const long long n = d.desc.plane;
+    const double* host[6] = {H, p, mx, my, C, Fs_prev};
+    double* buf = nullptr;
+    CK(cudaMalloc(&buf, sizeof(double) * n * 6), "state scratch");
+    const double* dev[6];
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 6; ++k) {
+        dev[k] = host[k] ? buf + k * n : nullptr;
+        if (host[k] && e == cudaSuccess)
+            e = cudaMemcpyAsync(buf + k * n, host[k], sizeof(double) * n, cudaMemcpyHostToDevice, s->stream);
+    }
+    if (e == cudaSuccess) e = launch_set_state(s->precision, d.d_desc, n, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5], s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(e, "set_state");
+    d.done = step;
+    if (d.finished()) s->dirty = true;
+    return EULBFS_OK;
+}
+
+unsigned long long eulbfs_checkpoint_bytes(const eulbfs_solver* s, int slot) {
+    if (check_slot(s, slot)) return 0;
+    const long long n = s->doms[slot].desc.plane;
+    return (unsigned long long)((planes_of(s->precision) + 1) * n * elem_of(s->precision));
+}
+
+int eulbfs_save(eulbfs_solver* s, int slot, void* buf, unsigned long long bytes, long long* step) {
+    int rc = check_slot(s, slot);
+    if (rc) return rc;
+    if (!buf || bytes != eulbfs_checkpoint_bytes(s, slot)) return fail(EULBFS_EINVAL, "checkpoint buffer size mismatch");
+    const Dom& d = s->doms[slot];
+    const size_t st = (size_t)planes_of(s->precision) * d.desc.plane * elem_of(s->precision);
+    const size_t fs = (size_t)d.desc.plane * elem_of(s->precision);
+    char* h = static_cast<char*>(buf);
+    CK(cudaMemcpyAsync(h, d.desc.st[0], st, cudaMemcpyDeviceToHost, s->stream), "save state");
+    CK(cudaMemcpyAsync(h + st, d.desc.Fsp, fs, cudaMemcpyDeviceToHost, s->stream), "save F_s");
+    CK(cudaStreamSynchronize(s->stream), "save sync");
+    if (step) *step = d.done;
+    return EULBFS_OK;
+}
+
+int eulbfs_load(eulbfs_solver* s, int slot, const void* buf, unsigned long long bytes, long long step) {
+    int rc = check_slot(s, slot);
+    if (rc) return rc;
+    if (!buf || bytes != eulbfs_checkpoint_bytes(s, slot)) return fail(EULBFS_EINVAL, "checkpoint buffer size mismatch");
+    if (step < 0) return fail(EULBFS_EINVAL, "step must be >= 0");
+    Dom& d = s->doms[slot];
+    const size_t st = (size_t)planes_of(s->precision) * d.desc.plane * elem_of(s->precision);
+    const size_t fs = (size_t)d.desc.plane * elem_of(s->precision);
+    const char* h = static_cast<const char*>(buf);
+    CK(cudaMemcpyAsync(d.desc.st[0], h, st, cudaMemcpyHostToDevice, s->stream), "load state");
+    CK(cudaMemcpyAsync(d.desc.Fsp, h + st, fs, cudaMemcpyHostToDevice, s->stream), "load F_s");
+    CK(cudaStreamSynchronize(s->stream), "load sync");
+    d.done = step;
+    if (d.finished()) s->dirty = true;
+    return EULBFS_OK;
+}
+
+int eulbfs_diagnostics(eulbfs_solver* s, int slot, eulbfs_diag* out) {
+    int rc = check_slot(s, slot);
+    if (rc) return rc;
+    if (!out) return fail(EULBFS_EINVAL, "null output");
+    const Dom& d = s->doms[slot];
+    const long long n = d.desc.plane;
+    const int nb = diag_blocks(n);
+    if (nb > s->partial_cap) {
+        CK(cudaStreamSynchronize(s->stream), "sync");
+        if (s->d_partial) cudaFree(s->d_partial);
+        s->partial_cap = std::max(nb, 64);
+        CK(cudaMalloc(&s->d_partial, sizeof(double) * kDiagFields * s->partial_cap), "diag scratch");
+    }
+    CK(launch_diag(s->precision, d.d_desc, n, s->d_partial, nb, s->d_diag, s->stream), "diag kernels");
+    CK(cudaMemcpyAsync(s->h_diag, s->d_diag, sizeof(double) * kDiagFields, cudaMemcpyDeviceToHost, s->stream), "diag copy");
+    const int sync_rc = eulbfs_sync(s);
+    if (sync_rc != EULBFS_OK && sync_rc != EULBFS_ENONFINITE) return sync_rc;
+    out->step = d.done;
+    out->t = d.done * d.num.dt;
+    out->mass = s->h_diag[0];
+    out->enthalpy = s->h_diag[1];
+    out->phase_vol = s->h_diag[2];
+    out->solid_vol = s->h_diag[3];
+    out->max_speed = s->h_diag[4];
+    out->nonfinite = s->h_diag[5] != 0.0 ? 1 : 0;
+    out->front_pos = out->solid_vol / d.grid.ny;
+    out->interface_pos = out->phase_vol / d.grid.ny;
+    if (out->nonfinite) return fail(EULBFS_ENONFINITE, "domain state is not finite");
+    return sync_rc;
+}
+
+void eulbfs_destroy(eulbfs_solver* s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    drop_graph(s);
+    for (Dom& d : s->doms)
+        if (d.mem) cudaFree(d.mem);
+    if (s->d_descs) cudaFree(s->d_descs);
+    if (s->d_tiles) cudaFree(s->d_tiles);
+    if (s->d_flag) cudaFree(s->d_flag);
+    if (s->h_flag) cudaFreeHost(s->h_flag);
+    if (s->d_partial) cudaFree(s->d_partial);
+    if (s->d_diag) cudaFree(s->d_diag);
+    if (s->h_diag) cudaFreeHost(s->h_diag);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+}  // extern "C"

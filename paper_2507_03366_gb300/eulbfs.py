@@ -1,0 +1,262 @@
+"""Thin ctypes binding of libeulbfs (include/eulbfs.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  If the library has not been built, or there is no CUDA device, the
+calls fail loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from .build import LIB as LIB_PATH
+
+FP64, FP32C = 0, 1
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EBUSY = range(7)
+_STATUS = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ENONFINITE: "ENONFINITE",
+           ETIMEOUT: "ETIMEOUT", EBUSY: "EBUSY"}
+
+
+class EulbfsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Grid(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int)]
+
+
+class Phase(ct.Structure):
+    _fields_ = [("rho", ct.c_double), ("mu", ct.c_double), ("lam", ct.c_double), ("cp", ct.c_double)]
+
+
+class Props(ct.Structure):
+    _fields_ = [("s", Phase), ("l", Phase), ("g", Phase), ("L", ct.c_double), ("Ts", ct.c_double),
+                ("Tl", ct.c_double), ("sigma", ct.c_double), ("xi", ct.c_double), ("Mc", ct.c_double),
+                ("tau_g", ct.c_double), ("gx", ct.c_double), ("gy", ct.c_double),
+                ("zero_solid_velocity", ct.c_int)]
+
+
+class Side(ct.Structure):
+    _fields_ = [("thermal", ct.c_int), ("flow", ct.c_int), ("phase", ct.c_int), ("Tw", ct.c_double),
+                ("theta_deg", ct.c_double)]
+
+
+class BC(ct.Structure):
+    _fields_ = [("xlo", Side), ("xhi", Side), ("ylo", Side), ("yhi", Side)]
+
+
+class Numerics(ct.Structure):
+    _fields_ = [("dt", ct.c_double)]
+
+
+_DP = ct.POINTER(ct.c_double)
+
+
+class Init(ct.Structure):
+    _fields_ = [("T", _DP), ("Fl", _DP), ("C", _DP), ("u", _DP), ("v", _DP), ("p", _DP)]
+
+
+class Domain(ct.Structure):
+    _fields_ = [("grid", Grid), ("props", Props), ("bc", BC), ("num", Numerics), ("init", Init)]
+
+
+class FieldsOut(ct.Structure):
+    _fields_ = [("H", _DP), ("T", _DP), ("Fl", _DP), ("C", _DP), ("p", _DP), ("u", _DP), ("v", _DP)]
+
+
+class Diag(ct.Structure):
+    _fields_ = [("step", ct.c_longlong), ("t", ct.c_double), ("mass", ct.c_double),
+                ("enthalpy", ct.c_double), ("phase_vol", ct.c_double), ("solid_vol", ct.c_double),
+                ("front_pos", ct.c_double), ("interface_pos", ct.c_double),
+                ("max_speed", ct.c_double), ("nonfinite", ct.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+# (name, restype, argtypes) of every entry point the header declares
+SIGNATURES = [
+    ("eulbfs_create", ct.c_int, [ct.POINTER(Grid), ct.POINTER(Props), ct.POINTER(BC), ct.POINTER(Numerics),
+                                 ct.POINTER(Init), ct.c_int, ct.c_void_p, ct.POINTER(ct.c_void_p)]),
+    ("eulbfs_batch_create", ct.c_int, [ct.c_int, ct.POINTER(Domain), ct.c_int, ct.c_void_p, ct.POINTER(ct.c_void_p)]),
+    ("eulbfs_set_memory_budget", ct.c_int, [ct.c_void_p, ct.c_ulonglong]),
+    ("eulbfs_domain_bytes", ct.c_ulonglong, [ct.c_int, ct.c_int, ct.c_int]),
+    ("eulbfs_add_domain", ct.c_int, [ct.c_void_p, ct.POINTER(Domain), ct.c_longlong, ct.POINTER(ct.c_int)]),
+    ("eulbfs_remove_domain", ct.c_int, [ct.c_void_p, ct.c_int]),
+    ("eulbfs_num_slots", ct.c_int, [ct.c_void_p]),
+    ("eulbfs_domain_progress", ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]),
+    ("eulbfs_step", ct.c_int, [ct.c_void_p, ct.c_longlong]),
+    ("eulbfs_sync", ct.c_int, [ct.c_void_p]),
+    ("eulbfs_fields", ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(FieldsOut)]),
+    ("eulbfs_get_state", ct.c_int, [ct.c_void_p, ct.c_int] + [_DP] * 7 + [ct.POINTER(ct.c_longlong)]),
+    ("eulbfs_set_state", ct.c_int, [ct.c_void_p, ct.c_int] + [_DP] * 6 + [ct.c_double, ct.c_longlong]),
+    ("eulbfs_checkpoint_bytes", ct.c_ulonglong, [ct.c_void_p, ct.c_int]),
+    ("eulbfs_save", ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_ulonglong, ct.POINTER(ct.c_longlong)]),
+    ("eulbfs_load", ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_ulonglong, ct.c_longlong]),
+    ("eulbfs_diagnostics", ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(Diag)]),
+    ("eulbfs_launches_per_step", ct.c_int, [ct.c_void_p]),
+    ("eulbfs_use_graphs", ct.c_int, [ct.c_void_p, ct.c_int]),
+    ("eulbfs_set_tile", ct.c_int, [ct.c_void_p, ct.c_int]),
+    ("eulbfs_destroy", None, [ct.c_void_p]),
+    ("eulbfs_last_error", ct.c_char_p, []),
+    ("eulbfs_version", ct.c_char_p, []),
+]
+
+
+def lib():
+    """Load libeulbfs.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; "
+                                   f"g.build()\"` (there is no CPU fallback)")
+            L = ct.CDLL(LIB_PATH)
+            for name, res, args in SIGNATURES:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise EulbfsError(rc, lib().eulbfs_last_error().decode())
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return a.ctypes.data_as(_DP) if a is not None else None
+
+
+def _props(p) -> Props:
+    ph = lambda q: Phase(q.rho, q.mu, q.lam, q.cp)  # noqa: E731
+    return Props(ph(p.s), ph(p.l), ph(p.g), p.L, p.Ts, p.Tl, p.sigma, p.xi, p.Mc, p.tau_g, p.gx, p.gy,
+                 int(p.zero_solid_velocity))
+
+
+def _bc(b) -> BC:
+    sd = lambda q: Side(q.thermal, q.flow, q.phase, q.Tw, q.theta_deg)  # noqa: E731
+    return BC(sd(b.xlo), sd(b.xhi), sd(b.ylo), sd(b.yhi))
+
+
+def domain_struct(case, keep: list) -> Domain:
+    """Marshal a workloads.Case into an eulbfs_domain (arrays kept alive in `keep`)."""
+    arrs = {k: np.ascontiguousarray(case.init[k], dtype=np.float64).ravel() for k in ("T", "Fl", "C", "u", "v", "p")}
+    keep.append(arrs)
+    init = Init(*[_ptr(arrs[k]) for k in ("T", "Fl", "C", "u", "v", "p")])
+    if abs(case.dt_stream - 0.5) > 0:
+        raise ValueError("libeulbfs uses the streaming step dt_s = 0.5 (lattice units)")
+    return Domain(Grid(case.nx, case.ny), _props(case.props), _bc(case.bc), Numerics(case.dt), init)
+
+
+class Solver:
+    """A set of domains advanced together on the GPU (eulbfs_solver)."""
+
+    def __init__(self, cases: Sequence, precision: int = FP32C, stream: Optional[int] = None):
+        cases = list(cases)
+        keep: list = []
+        arr = (Domain * len(cases))(*[domain_struct(c, keep) for c in cases])
+        h = ct.c_void_p()
+        _check(lib().eulbfs_batch_create(len(cases), arr, precision, ct.c_void_p(stream) if stream else None,
+                                         ct.byref(h)))
+        self._h = h
+        self.precision = precision
+        self.shapes: List = [(c.ny, c.nx) for c in cases]
+        self.cases = cases
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.eulbfs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    # -- continuous batching
+    def add(self, case, max_steps: int = 0) -> int:
+        keep: list = []
+        d = domain_struct(case, keep)
+        slot = ct.c_int()
+        _check(lib().eulbfs_add_domain(self._h, ct.byref(d), max_steps, ct.byref(slot)))
+        while len(self.shapes) <= slot.value:
+            self.shapes.append(None)
+            self.cases.append(None)
+        self.shapes[slot.value] = (case.ny, case.nx)
+        self.cases[slot.value] = case
+        return slot.value
+
+    def remove(self, slot: int):
+        _check(lib().eulbfs_remove_domain(self._h, slot))
+
+    def progress(self, slot: int):
+        done, left = ct.c_longlong(), ct.c_longlong()
+        _check(lib().eulbfs_domain_progress(self._h, slot, ct.byref(done), ct.byref(left)))
+        return done.value, left.value
+
+    def set_memory_budget(self, nbytes: int):
+        _check(lib().eulbfs_set_memory_budget(self._h, nbytes))
+
+    # -- stepping
+    def step(self, n: int = 1):
+        _check(lib().eulbfs_step(self._h, n))
+
+    def sync(self):
+        _check(lib().eulbfs_sync(self._h))
+
+    def use_graphs(self, steps: int):
+        _check(lib().eulbfs_use_graphs(self._h, steps))
+
+    def set_tile(self, tile_y: int):
+        _check(lib().eulbfs_set_tile(self._h, tile_y))
+
+    def launches_per_step(self) -> int:
+        return lib().eulbfs_launches_per_step(self._h)
+
+    # -- outputs
+    def fields(self, slot: int = 0, which=("H", "T", "Fl", "C", "p", "u", "v")) -> dict:
+        ny, nx = self.shapes[slot]
+        out = {k: np.empty(nx * ny) for k in which}
+        fo = FieldsOut(*[_ptr(out.get(k)) for k in ("H", "T", "Fl", "C", "p", "u", "v")])
+        _check(lib().eulbfs_fields(self._h, slot, ct.byref(fo)))
+        return {k: v.reshape(ny, nx) for k, v in out.items()}
+
+    def state(self, slot: int = 0) -> dict:
+        ny, nx = self.shapes[slot]
+        out = {k: np.empty(nx * ny) for k in ("H", "p", "mx", "my", "C", "Fsp")}
+        t, step = ct.c_double(), ct.c_longlong()
+        _check(lib().eulbfs_get_state(self._h, slot, *[_ptr(out[k]) for k in ("H", "p", "mx", "my", "C", "Fsp")],
+                                      ct.byref(t), ct.byref(step)))
+        res = {k: v.reshape(ny, nx) for k, v in out.items()}
+        res["t"], res["step"] = t.value, step.value
+        return res
+
+    def set_state(self, st: dict, slot: int = 0):
+        arrs = [np.ascontiguousarray(st[k], dtype=np.float64).ravel() for k in ("H", "p", "mx", "my", "C", "Fsp")]
+        _check(lib().eulbfs_set_state(self._h, slot, *[_ptr(a) for a in arrs], float(st.get("t", 0.0)),
+                                      int(st.get("step", 0))))
+
+    def save(self, slot: int = 0):
+        """Bitwise-exact checkpoint: (bytes, step)."""
+        n = lib().eulbfs_checkpoint_bytes(self._h, slot)
+        buf = ct.create_string_buffer(n)
+        step = ct.c_longlong()
+        _check(lib().eulbfs_save(self._h, slot, buf, n, ct.byref(step)))
+        return buf.raw, step.value
+
+    def load(self, blob: bytes, step: int, slot: int = 0):
+        _check(lib().eulbfs_load(self._h, slot, blob, len(blob), step))
+
+    def diag(self, slot: int = 0) -> dict:
+        d = Diag()
+        _check(lib().eulbfs_diagnostics(self._h, slot, ct.byref(d)))
+        return d.as_dict()

@@ -1,0 +1,72 @@
+"""The C-ABI library builds, loads and exports every entry point of
+include/eulbfs.h; on a machine without a GPU it refuses to run instead of
+falling back to the CPU."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+from paper_2507_03366_gb300 import build as B
+from paper_2507_03366_gb300 import eulbfs
+from paper_2507_03366_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "eulbfs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(eulbfs_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return eulbfs.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    # the binding wraps exactly the declared entry points
+    assert sorted(n for n, _, _ in eulbfs.SIGNATURES) == names
+
+
+def test_version_and_sizes(lib):
+    assert b"sm_103a" in lib.eulbfs_version()
+    # 3 state buffers x 7 FP32 planes + 2 FP32 planes per cell, plus a descriptor
+    n = 128 * 64
+    assert lib.eulbfs_domain_bytes(128, 64, eulbfs.FP32C) >= n * (3 * 7 * 4 + 2 * 4)
+    assert lib.eulbfs_domain_bytes(128, 64, eulbfs.FP64) >= n * (3 * 5 * 8 + 2 * 8)
+    assert lib.eulbfs_domain_bytes(0, 64, eulbfs.FP64) == 0
+
+
+def test_no_cpu_fallback_without_gpu(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(eulbfs.EulbfsError) as e:
+        eulbfs.Solver([wl.conductive(32, 2)], precision=eulbfs.FP64)
+    assert e.value.code in (eulbfs.ECUDA,)
+
+
+def test_invalid_arguments_rejected_before_device_work(lib):
+    h = ct.c_void_p()
+    # null domain list
+    assert lib.eulbfs_batch_create(0, None, eulbfs.FP32C, None, ct.byref(h)) == eulbfs.EINVAL
+    # tau_g <= 0.5 is invalid (Sec. 2.3.2: M_c = (tau_g - 0.5) Q_g dt_s)
+    case = wl.conductive(32, 2)
+    case.props.tau_g = 0.5
+    keep = []
+    d = eulbfs.domain_struct(case, keep)
+    assert lib.eulbfs_batch_create(1, ct.byref(d), eulbfs.FP32C, None, ct.byref(h)) == eulbfs.EINVAL
+    assert b"tau_g" in lib.eulbfs_last_error()
+    # periodic on one side only
+    case = wl.conductive(32, 2)
+    case.bc.yhi = wl.Side(wl.ADIABATIC, wl.NOSLIP, wl.NOFLUX)
+    d = eulbfs.domain_struct(case, keep)
+    assert lib.eulbfs_batch_create(1, ct.byref(d), eulbfs.FP64, None, ct.byref(h)) == eulbfs.EINVAL
+    assert lib.eulbfs_step(None, 1) == eulbfs.EINVAL
