@@ -201,6 +201,35 @@ int eulbfs_use_graphs(eulbfs_solver* s, int steps_per_graph);
 /* Tile shape (cells) of the stage kernel; 0 = the default. */
 int eulbfs_set_tile(eulbfs_solver* s, int tile_y);
 
+/* Diagnostics of a caller-held domain state that allocates no device memory.
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot let a library call cudaMalloc or cudaFree: programs whose device
+ * memory is fully committed to another framework's allocator, and loops that
+ * cannot afford cudaFree's device-wide synchronisation or a driver allocation
+ * in the middle of a step.  It computes what eulbfs_diagnostics computes.
+ *   state: device pointer to the conserved-state planes of one domain in the
+ *          working precision, nx*ny values per plane, planes back to back:
+ *          FP64 5 planes of doubles (H, p, rho cs^2 u, rho cs^2 v, C); FP32C
+ *          7 planes of floats (H_hi, H_lo, p, m_x, m_y, C_hi, C_lo), e.g. the
+ *          first part of an eulbfs_save buffer copied to the device.
+ *   props: host struct of the domain's properties (used for rho and F_s).
+ *   out:   device pointer to 6 doubles: mass, enthalpy, phase_vol, solid_vol,
+ *          max_speed, nonfinite (1.0 or 0.0).
+ *   stream: cudaStream_t to enqueue on (NULL: the legacy default stream);
+ *          the call returns after enqueueing.
+ * Limit: nx*ny <= EULBFS_NOALLOC_MAX_CELLS; larger domains return EINVAL.
+ * The block partials live in one fixed 48 KiB device array inside the
+ * library (1024 x 6 doubles), held on every GPU that loads the library until
+ * the process exits and shared by all calls: each call overwrites the
+ * partials it uses, so nothing needs clearing, but calls that overlap on the
+ * GPU (different streams or host threads) race on it and must be serialised.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. */
+#define EULBFS_NOALLOC_MAX_CELLS 2097152
+int eulbfs_diagnostics_noalloc(int precision, const void* state, int nx, int ny,
+                               const eulbfs_props* props, double* out, void* stream);
+
 void eulbfs_destroy(eulbfs_solver* s);
 
 /* Message of the last failed call on this thread ("" if none). */

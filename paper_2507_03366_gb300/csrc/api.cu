@@ -136,6 +136,8 @@ size_t domain_bytes(long long n, int precision) {
 
 }  // namespace
 
+int eulbfs::set_error(int code, const char* msg) { return fail(code, msg); }
+
 struct eulbfs_solver {
     int precision = EULBFS_FP32C;
     cudaStream_t stream = nullptr;

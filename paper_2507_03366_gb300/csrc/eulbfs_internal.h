@@ -80,4 +80,7 @@ int diag_blocks(long long n);
 cudaError_t launch_diag(int precision, const DomainDesc* d_desc, long long n, double* partial,
                         int nblocks, double* out, cudaStream_t s);
 
+// Record the message returned by eulbfs_last_error() on this thread.
+int set_error(int code, const char* msg);
+
 }  // namespace eulbfs

@@ -24,6 +24,9 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
+#include "eulbfs.h"
 #include "eulbfs_internal.h"
 
 namespace eulbfs {
@@ -785,3 +788,122 @@ cudaError_t launch_diag(int precision, const DomainDesc* d, long long n, double*
 }
 
 }  // namespace eulbfs
+
+// ---------------------------------------------------------------------------
+// Diagnostics of a caller-held state without any device allocation.
+//
+// Some callers cannot let a library call cudaMalloc / cudaFree: programs whose
+// device memory is fully committed to another framework's pool, and loops
+// that cannot afford the implicit device synchronisation of cudaFree or a
+// driver allocation in the middle of a latency-bound step.  For them the
+// block partials of the diagnostics reduction live in this fixed, file-scope
+// device array instead of a buffer from cudaMalloc.  Every GPU that loads the
+// library holds the array (kNoAllocMaxBlocks x 6 doubles = 48 KiB) until the
+// process exits.  All calls share it: each call overwrites exactly the
+// partials it reads back, so nothing has to start at zero, but two calls that
+// overlap on the GPU (different streams, or different host threads) race on
+// it and must be serialised by the caller.
+// ---------------------------------------------------------------------------
+namespace eulbfs {
+
+constexpr int kNoAllocMaxBlocks = 1024;
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * kDiagFields];
+
+template <class R>
+__global__ void __launch_bounds__(kDiagThreads)
+diag_partial_noalloc_kernel(Consts<double> Kd, const R* b, long long n, double* partial) {
+    __shared__ double red[kDiagThreads / 32][kDiagFields];
+    double acc[kDiagFields] = {0, 0, 0, 0, 0, 0};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const SV<R> w = load_state(b, n, c);
+        const double H = pair_value(w.Hh, w.Hl), C = pair_value(w.Ch, w.Cl);
+        double T, Fl;
+        invert_enthalpy(Kd, H, 0.0, clamp01(C), T, Fl);
+        const double rho = mix(clamp01(C), Fl, Kd.rho);
+        acc[0] += rho;
+        acc[1] += H;
+        acc[2] += C;
+        acc[3] += clamp01(C) * (1.0 - Fl);
+        const double mx = (double)w.mx, my = (double)w.my;
+        acc[4] = fmax(acc[4], sqrt(mx * mx + my * my) / (rho * (1.0 / 3.0)));
+        if (!(isfinite(H) && isfinite(C) && isfinite((double)w.p) && isfinite(mx) && isfinite(my))) acc[5] = 1.0;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kDiagFields; ++k) {
+        const double r = (k == 4 || k == 5) ? warp_max(acc[k]) : warp_sum(acc[k]);
+        if (lane == 0) red[wid][k] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x < kDiagFields) {
+        const int k = threadIdx.x;
+        double r = red[0][k];
+        for (int w2 = 1; w2 < kDiagThreads / 32; ++w2) r = (k == 4 || k == 5) ? fmax(r, red[w2][k]) : r + red[w2][k];
+        partial[(long long)blockIdx.x * kDiagFields + k] = r;
+    }
+}
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_partials on the current device.  In host code
+// the array's name is only a host-side stand-in, never a device address, so
+// the address is resolved once per device (with that device current).
+int noalloc_scratch(double** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_error(EULBFS_ECUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return set_error(EULBFS_ECUDA, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return set_error(EULBFS_ECUDA, "cudaGetSymbolAddress of the diagnostics scratch array failed");
+        }
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return EULBFS_OK;
+}
+}  // namespace
+
+}  // namespace eulbfs
+
+extern "C" int eulbfs_diagnostics_noalloc(int precision, const void* state, int nx, int ny, const eulbfs_props* props,
+                                          double* out, void* stream) {
+    using namespace eulbfs;
+    if (precision != EULBFS_FP64 && precision != EULBFS_FP32C) return set_error(EULBFS_EINVAL, "unknown precision");
+    if (!state || !out || !props) return set_error(EULBFS_EINVAL, "state, props and out must be non-null");
+    if (nx < 1 || ny < 1) return set_error(EULBFS_EINVAL, "nx and ny must be >= 1");
+    const long long n = (long long)nx * ny;
+    const int nb = diag_blocks(n);
+    if (n > EULBFS_NOALLOC_MAX_CELLS || nb > kNoAllocMaxBlocks)
+        return set_error(EULBFS_EINVAL, "domain exceeds the no-allocation diagnostics limit of "
+                                        "EULBFS_NOALLOC_MAX_CELLS (2097152) cells");
+    double* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != EULBFS_OK) return rc;
+    Consts<double> Kd = {};
+    const eulbfs_phase* ph[3] = {&props->s, &props->l, &props->g};
+    for (int k = 0; k < 3; ++k) { Kd.rho[k] = ph[k]->rho; Kd.cp[k] = ph[k]->cp; }
+    Kd.Ts = props->Ts;
+    Kd.Tl = props->Tl;
+    Kd.L = props->L;
+    Kd.plane = n;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == EULBFS_FP64)
+        diag_partial_noalloc_kernel<double><<<nb, kDiagThreads, 0, s>>>(Kd, static_cast<const double*>(state), n, scratch);
+    else
+        diag_partial_noalloc_kernel<float><<<nb, kDiagThreads, 0, s>>>(Kd, static_cast<const float*>(state), n, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        diag_final_kernel<<<1, 32, 0, s>>>(scratch, nb, out);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return set_error(EULBFS_ECUDA, cudaGetErrorString(e));
+    return EULBFS_OK;
+}

@@ -106,6 +106,8 @@ SIGNATURES = [
     ("eulbfs_launches_per_step", ct.c_int, [ct.c_void_p]),
     ("eulbfs_use_graphs", ct.c_int, [ct.c_void_p, ct.c_int]),
     ("eulbfs_set_tile", ct.c_int, [ct.c_void_p, ct.c_int]),
+    ("eulbfs_diagnostics_noalloc", ct.c_int, [ct.c_int, ct.c_void_p, ct.c_int, ct.c_int, ct.POINTER(Props),
+                                              ct.c_void_p, ct.c_void_p]),
     ("eulbfs_destroy", None, [ct.c_void_p]),
     ("eulbfs_last_error", ct.c_char_p, []),
     ("eulbfs_version", ct.c_char_p, []),
