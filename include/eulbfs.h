@@ -126,9 +126,10 @@ int eulbfs_create(const eulbfs_grid* grid, const eulbfs_props* props, const eulb
                   const eulbfs_numerics* num, const eulbfs_init* init, int precision,
                   void* stream, eulbfs_solver** out);
 
-/* Create a solver holding n >= 1 domains of any sizes and parameters that
+/* Create a solver holding n >= 0 domains of any sizes and parameters that
  * advance together: every stage of every domain runs in one launch over a
- * tile work list (configs with many uneven domains). */
+ * work list of strip segments (many uneven domains).  n = 0 creates an empty
+ * solver that eulbfs_add_domain fills (a serving loop). */
 int eulbfs_batch_create(int n, const eulbfs_domain* domains, int precision, void* stream,
                         eulbfs_solver** out);
 
@@ -164,7 +165,8 @@ int eulbfs_step(eulbfs_solver* s, long long n);
 int eulbfs_sync(eulbfs_solver* s);
 
 /* Copy primitive fields of domain `slot` to caller-owned host arrays
- * (synchronises the solver's stream). */
+ * (synchronises the solver's stream).  Returns ENONFINITE (after copying) if
+ * this domain produced a NaN or Inf; other domains do not affect it. */
 int eulbfs_fields(eulbfs_solver* s, int slot, const eulbfs_fields_out* out);
 
 /* Conserved state W = (H, p, rho cs^2 u, rho cs^2 v, C) (Eq. 49), the
@@ -188,7 +190,8 @@ unsigned long long eulbfs_checkpoint_bytes(const eulbfs_solver* s, int slot);
 int eulbfs_save(eulbfs_solver* s, int slot, void* buf, unsigned long long bytes, long long* step);
 int eulbfs_load(eulbfs_solver* s, int slot, const void* buf, unsigned long long bytes, long long step);
 
-/* FP64 diagnostics of domain `slot` (synchronises the solver's stream). */
+/* FP64 diagnostics of domain `slot` (synchronises the solver's stream);
+ * ENONFINITE (with d filled) if this domain's state is not finite. */
 int eulbfs_diagnostics(eulbfs_solver* s, int slot, eulbfs_diag* d);
 
 /* Number of kernels the solver launches per time step of the current batch. */
@@ -198,8 +201,10 @@ int eulbfs_launches_per_step(const eulbfs_solver* s);
  * steps (0 disables); replays are used when n is a multiple of it. */
 int eulbfs_use_graphs(eulbfs_solver* s, int steps_per_graph);
 
-/* Tile shape (cells) of the stage kernel; 0 = the default. */
-int eulbfs_set_tile(eulbfs_solver* s, int tile_y);
+/* Work-item shape of the stage kernel: each item is a 31-column strip of a
+ * domain, `rows` cells high (a multiple of 8 in [8, 1024]; 0 = 64).  Results
+ * do not depend on it. */
+int eulbfs_set_tile(eulbfs_solver* s, int rows);
 
 /* Diagnostics of a caller-held domain state that allocates no device memory.
  * The paper has no counterpart to this call; it exists for callers that
@@ -229,6 +234,13 @@ int eulbfs_set_tile(eulbfs_solver* s, int tile_y);
 #define EULBFS_NOALLOC_MAX_CELLS 2097152
 int eulbfs_diagnostics_noalloc(int precision, const void* state, int nx, int ny,
                                const eulbfs_props* props, double* out, void* stream);
+
+/* Pick the work-item height of the current batch by timing each candidate
+ * (16, 32, 64, 128, 256 rows) over steps_per_candidate steps on the solver's
+ * stream and keeping the fastest.  The timed steps are real steps of every
+ * active domain (results do not depend on the height), so the simulation
+ * advances by 5 * (steps_per_candidate + 1) steps.  Synchronises the stream. */
+int eulbfs_autotune(eulbfs_solver* s, int steps_per_candidate, int* best_rows, float* best_ms_per_step);
 
 void eulbfs_destroy(eulbfs_solver* s);
 

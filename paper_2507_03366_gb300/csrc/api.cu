@@ -131,7 +131,8 @@ DomainDesc make_desc(const eulbfs_grid& g, const eulbfs_props& P, const eulbfs_b
 
 size_t domain_bytes(long long n, int precision) {
     const size_t e = elem_of(precision);
-    return align256(sizeof(DomainDesc)) + 3 * align256((size_t)planes_of(precision) * n * e) + 2 * align256(n * e);
+    return align256(sizeof(DomainDesc)) + 256 /* flag */ + 3 * align256((size_t)planes_of(precision) * n * e) +
+           2 * align256(n * e);
 }
 
 }  // namespace
@@ -143,13 +144,13 @@ struct eulbfs_solver {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::vector<Dom> doms;
-    DomainDesc* d_descs = nullptr;
-    int descs_cap = 0;
-    int* d_tiles = nullptr;
-    int tiles_cap = 0;
-    int ntiles = 0;
+    void* d_consts = nullptr;      // Consts<R>[ndomains] in the working precision
+    size_t consts_cap = 0;
+    int4* d_items = nullptr;       // work items (domain, strip, segment, 0)
+    int items_cap = 0;
+    int nitems = 0;
     bool dirty = true;
-    int tile_y = 8;
+    int seg = 64;                  // segment height of a work item (rows)
     int sms = 1;
     int grid = 1;
     int* d_flag = nullptr;
@@ -173,35 +174,49 @@ void drop_graph(eulbfs_solver* s) {
     s->graph_valid = false;
 }
 
+template <class R>
+std::vector<unsigned char> consts_image(const std::vector<Dom>& doms) {
+    std::vector<unsigned char> img(sizeof(Consts<R>) * doms.size());
+    for (size_t k = 0; k < doms.size(); ++k) {
+        Consts<R> K{};
+        fill_consts(doms[k].desc, K);
+        std::memcpy(img.data() + k * sizeof(Consts<R>), &K, sizeof(K));
+    }
+    return img;
+}
+
+// Rebuild the work list (strip segments of every active domain) and the
+// per-domain constants after the set of domains or the segment height changed.
 int rebuild(eulbfs_solver* s) {
     const int nd = (int)s->doms.size();
-    if (nd > s->descs_cap) {
-        if (s->d_descs) cudaFree(s->d_descs);
-        s->descs_cap = std::max(nd, 2 * s->descs_cap);
-        CK(cudaMalloc(&s->d_descs, sizeof(DomainDesc) * s->descs_cap), "descriptor array");
+    std::vector<unsigned char> img =
+        s->precision == EULBFS_FP64 ? consts_image<double>(s->doms) : consts_image<float>(s->doms);
+    if (img.size() > s->consts_cap) {
+        if (s->d_consts) cudaFree(s->d_consts);
+        s->consts_cap = std::max(img.size(), 2 * s->consts_cap);
+        CK(cudaMalloc(&s->d_consts, s->consts_cap), "constants array");
     }
-    std::vector<int> tiles;
-    std::vector<DomainDesc> descs(nd);
+    std::vector<int4> items;
     for (int k = 0; k < nd; ++k) {
         Dom& d = s->doms[k];
-        d.desc.tiles_x = (d.grid.nx + kTileX - 1) / kTileX;
-        d.desc.tiles_y = (d.grid.ny + s->tile_y - 1) / s->tile_y;
-        d.desc.tile0 = (int)tiles.size();
-        if (d.active()) tiles.insert(tiles.end(), (size_t)d.desc.tiles_x * d.desc.tiles_y, k);
-        descs[k] = d.desc;
+        d.desc.strips = (d.grid.nx + kStripX - 1) / kStripX;
+        d.desc.segs = (d.grid.ny + s->seg - 1) / s->seg;
+        if (!d.active()) continue;
+        for (int sy = 0; sy < d.desc.segs; ++sy)
+            for (int sx = 0; sx < d.desc.strips; ++sx) items.push_back(make_int4(k, sx, sy, 0));
     }
-    if (nd) CK(cudaMemcpyAsync(s->d_descs, descs.data(), sizeof(DomainDesc) * nd, cudaMemcpyHostToDevice, s->stream), "upload descriptors");
-    s->ntiles = (int)tiles.size();
-    if (s->ntiles > s->tiles_cap) {
-        if (s->d_tiles) cudaFree(s->d_tiles);
-        s->tiles_cap = std::max(s->ntiles, 2 * s->tiles_cap);
-        CK(cudaMalloc(&s->d_tiles, sizeof(int) * s->tiles_cap), "tile list");
+    if (!img.empty()) CK(cudaMemcpyAsync(s->d_consts, img.data(), img.size(), cudaMemcpyHostToDevice, s->stream), "upload constants");
+    s->nitems = (int)items.size();
+    if (s->nitems > s->items_cap) {
+        if (s->d_items) cudaFree(s->d_items);
+        s->items_cap = std::max(s->nitems, 2 * s->items_cap);
+        CK(cudaMalloc(&s->d_items, sizeof(int4) * s->items_cap), "work list");
     }
-    if (s->ntiles) CK(cudaMemcpyAsync(s->d_tiles, tiles.data(), sizeof(int) * s->ntiles, cudaMemcpyHostToDevice, s->stream), "upload tiles");
+    if (s->nitems) CK(cudaMemcpyAsync(s->d_items, items.data(), sizeof(int4) * s->nitems, cudaMemcpyHostToDevice, s->stream), "upload work list");
     // the host vectors die here: make the copies complete before returning
     CK(cudaStreamSynchronize(s->stream), "rebuild sync");
-    const int per_sm = stage_blocks_per_sm(s->precision, s->tile_y);
-    s->grid = std::max(1, std::min(s->ntiles, per_sm * s->sms));
+    const int per_sm = stage_blocks_per_sm(s->precision);
+    s->grid = std::max(1, std::min(s->nitems, per_sm * s->sms));
     drop_graph(s);
     s->dirty = false;
     return EULBFS_OK;
@@ -209,13 +224,14 @@ int rebuild(eulbfs_solver* s) {
 
 int launch_step_direct(eulbfs_solver* s) {
     StageLaunch a;
-    a.descs = s->d_descs;
-    a.tile_domain = s->d_tiles;
-    a.ntiles = s->ntiles;
+    a.consts = s->d_consts;
+    a.items = s->d_items;
+    a.nitems = s->nitems;
+    a.seg = s->seg;
     a.flag = s->d_flag;
     for (int st = 0; st < 3; ++st) {
         a.stage = st;
-        cudaError_t e = launch_stage(s->precision, s->tile_y, a, s->grid, s->stream);
+        cudaError_t e = launch_stage(s->precision, a, s->grid, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
     }
     return EULBFS_OK;
@@ -244,6 +260,14 @@ int capture_graph(eulbfs_solver* s) {
         return EULBFS_ECUDA;
     }
     s->graph_valid = true;
+    return EULBFS_OK;
+}
+
+// 1 if the domain's own non-finite flag is set (synchronises the stream).
+int domain_nonfinite(eulbfs_solver* s, const Dom& d, int* out) {
+    CK(cudaMemcpyAsync(s->h_flag, d.desc.flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "flag copy");
+    CK(cudaStreamSynchronize(s->stream), "stream sync");
+    *out = *s->h_flag & 1;
     return EULBFS_OK;
 }
 
@@ -278,6 +302,8 @@ int add_domain(eulbfs_solver* s, const eulbfs_domain& dm, long long max_steps, i
     char* p = static_cast<char*>(d.mem);
     d.d_desc = reinterpret_cast<DomainDesc*>(p);
     p += align256(sizeof(DomainDesc));
+    d.desc.flag = reinterpret_cast<int*>(p);
+    p += 256;
     const size_t e = elem_of(s->precision);
     for (int k = 0; k < 3; ++k) {
         d.desc.st[k] = p;
@@ -388,7 +414,7 @@ int eulbfs_create(const eulbfs_grid* grid, const eulbfs_props* props, const eulb
 }
 
 int eulbfs_batch_create(int n, const eulbfs_domain* domains, int precision, void* stream, eulbfs_solver** out) {
-    if (n < 1 || !domains) return fail(EULBFS_EINVAL, "need at least one domain");
+    if (n < 0 || (n > 0 && !domains)) return fail(EULBFS_EINVAL, "need n >= 0 domains");
     if (!out) return fail(EULBFS_EINVAL, "out is null");
     for (int k = 0; k < n; ++k) {
         int rc = validate(domains[k].grid, domains[k].props, domains[k].bc, domains[k].num);
@@ -444,14 +470,51 @@ int eulbfs_domain_progress(const eulbfs_solver* s, int slot, long long* done, lo
     return EULBFS_OK;
 }
 
-int eulbfs_set_tile(eulbfs_solver* s, int tile_y) {
+int eulbfs_set_tile(eulbfs_solver* s, int rows) {
     if (!s) return fail(EULBFS_EINVAL, "null solver");
-    if (tile_y == 0) tile_y = 8;
-    if (tile_y != 4 && tile_y != 8 && tile_y != 16) return fail(EULBFS_EINVAL, "tile_y must be 4, 8 or 16");
-    if (tile_y != s->tile_y) {
-        s->tile_y = tile_y;
+    if (rows == 0) rows = 64;
+    if (rows < kChunk || rows > 1024 || rows % kChunk) return fail(EULBFS_EINVAL, "segment height must be a multiple of 8 in [8, 1024]");
+    if (rows != s->seg) {
+        s->seg = rows;
         s->dirty = true;
     }
+    return EULBFS_OK;
+}
+
+int eulbfs_autotune(eulbfs_solver* s, int steps_per_candidate, int* best_rows, float* best_ms_per_step) {
+    if (!s) return fail(EULBFS_EINVAL, "null solver");
+    if (steps_per_candidate < 1) return fail(EULBFS_EINVAL, "steps_per_candidate must be >= 1");
+    static const int kCandidates[] = {16, 32, 64, 128, 256};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    const int saved_graph = s->graph_steps;
+    s->graph_steps = 0;                      // time the launches themselves
+    int best = s->seg;
+    float best_ms = 0.f;
+    int rc = EULBFS_OK;
+    for (int rows : kCandidates) {
+        rc = eulbfs_set_tile(s, rows);
+        if (rc == EULBFS_OK) rc = eulbfs_step(s, 1);   // rebuild + warm the work list
+        if (rc != EULBFS_OK) break;
+        if (s->nitems == 0) break;                     // nothing to time
+        cudaEventRecord(e0, s->stream);
+        rc = eulbfs_step(s, steps_per_candidate);
+        cudaEventRecord(e1, s->stream);
+        if (rc != EULBFS_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "autotune timing"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= steps_per_candidate;
+        if (best_ms == 0.f || ms < best_ms) { best_ms = ms; best = rows; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->graph_steps = saved_graph;
+    if (rc != EULBFS_OK) return rc;
+    eulbfs_set_tile(s, best);
+    if (best_rows) *best_rows = best;
+    if (best_ms_per_step) *best_ms_per_step = best_ms;
     return EULBFS_OK;
 }
 
@@ -473,7 +536,7 @@ int eulbfs_step(eulbfs_solver* s, long long n) {
             int rc = rebuild(s);
             if (rc) return rc;
         }
-        if (s->ntiles == 0) break;
+        if (s->nitems == 0) break;
         long long k = n;
         for (const Dom& d : s->doms)
             if (d.active() && d.max_steps > 0) k = std::min(k, d.max_steps - d.done);
@@ -524,7 +587,10 @@ int eulbfs_fields(eulbfs_solver* s, int slot, const eulbfs_fields_out* out) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     cudaFree(buf);
     if (e != cudaSuccess) return cuda_fail(e, "fields");
-    return eulbfs_sync(s) == EULBFS_ENONFINITE ? EULBFS_ENONFINITE : EULBFS_OK;
+    int bad = 0;
+    rc = domain_nonfinite(s, d, &bad);
+    if (rc) return rc;
+    return bad ? fail(EULBFS_ENONFINITE, "this domain produced a non-finite state") : EULBFS_OK;
 }
 
 int eulbfs_get_state(eulbfs_solver* s, int slot, double* H, double* p, double* mx, double* my, double* C,
@@ -629,8 +695,9 @@ int eulbfs_diagnostics(eulbfs_solver* s, int slot, eulbfs_diag* out) {
     }
     CK(launch_diag(s->precision, d.d_desc, n, s->d_partial, nb, s->d_diag, s->stream), "diag kernels");
     CK(cudaMemcpyAsync(s->h_diag, s->d_diag, sizeof(double) * kDiagFields, cudaMemcpyDeviceToHost, s->stream), "diag copy");
-    const int sync_rc = eulbfs_sync(s);
-    if (sync_rc != EULBFS_OK && sync_rc != EULBFS_ENONFINITE) return sync_rc;
+    int bad = 0;
+    rc = domain_nonfinite(s, d, &bad);   // synchronises the stream
+    if (rc) return rc;
     out->step = d.done;
     out->t = d.done * d.num.dt;
     out->mass = s->h_diag[0];
@@ -641,8 +708,11 @@ int eulbfs_diagnostics(eulbfs_solver* s, int slot, eulbfs_diag* out) {
     out->nonfinite = s->h_diag[5] != 0.0 ? 1 : 0;
     out->front_pos = out->solid_vol / d.grid.ny;
     out->interface_pos = out->phase_vol / d.grid.ny;
-    if (out->nonfinite) return fail(EULBFS_ENONFINITE, "domain state is not finite");
-    return sync_rc;
+    if (out->nonfinite || bad) {
+        out->nonfinite = 1;
+        return fail(EULBFS_ENONFINITE, "domain state is not finite");
+    }
+    return EULBFS_OK;
 }
 
 void eulbfs_destroy(eulbfs_solver* s) {
@@ -651,8 +721,8 @@ void eulbfs_destroy(eulbfs_solver* s) {
     drop_graph(s);
     for (Dom& d : s->doms)
         if (d.mem) cudaFree(d.mem);
-    if (s->d_descs) cudaFree(s->d_descs);
-    if (s->d_tiles) cudaFree(s->d_tiles);
+    if (s->d_consts) cudaFree(s->d_consts);
+    if (s->d_items) cudaFree(s->d_items);
     if (s->d_flag) cudaFree(s->d_flag);
     if (s->h_flag) cudaFreeHost(s->h_flag);
     if (s->d_partial) cudaFree(s->d_partial);

@@ -1,0 +1,149 @@
+// device_common.cuh -- device helpers shared by the stage kernel and the
+// auxiliary kernels of libeulbfs: state access, compensated sums, the
+// enthalpy closure (Eq. 5-7), boundary mapping and the derived fields.
+#pragma once
+#include <math.h>
+#include <stdint.h>
+
+#include "eulbfs_internal.h"
+
+namespace eulbfs {
+
+enum { BC_PERIODIC = 0, BC_DIRICHLET_T, BC_ADIABATIC, BC_NOSLIP, BC_SYMMETRY, BC_OUTLET, BC_NOFLUX, BC_WETTING };
+
+template <class R> struct Prec;
+template <> struct Prec<double> { static constexpr int NP = 5; };
+template <> struct Prec<float> { static constexpr int NP = 7; };
+
+// ---------------------------------------------------------------------------
+// State access.  FP64: H p mx my C.  FP32C: Hhi Hlo p mx my Chi Clo.
+// ---------------------------------------------------------------------------
+template <class R>
+struct SV { R Hh, Hl, p, mx, my, Ch, Cl; };
+
+__device__ __forceinline__ SV<double> load_state(const double* b, long long P, long long c) {
+    SV<double> s;
+    s.Hh = b[c]; s.Hl = 0.0; s.p = b[P + c]; s.mx = b[2 * P + c]; s.my = b[3 * P + c];
+    s.Ch = b[4 * P + c]; s.Cl = 0.0;
+    return s;
+}
+__device__ __forceinline__ SV<float> load_state(const float* b, long long P, long long c) {
+    SV<float> s;
+    s.Hh = b[c]; s.Hl = b[P + c]; s.p = b[2 * P + c]; s.mx = b[3 * P + c]; s.my = b[4 * P + c];
+    s.Ch = b[5 * P + c]; s.Cl = b[6 * P + c];
+    return s;
+}
+__device__ __forceinline__ void store_state(double* b, long long P, long long c, const SV<double>& s) {
+    b[c] = s.Hh; b[P + c] = s.p; b[2 * P + c] = s.mx; b[3 * P + c] = s.my; b[4 * P + c] = s.Ch;
+}
+__device__ __forceinline__ void store_state(float* b, long long P, long long c, const SV<float>& s) {
+    b[c] = s.Hh; b[P + c] = s.Hl; b[2 * P + c] = s.p; b[3 * P + c] = s.mx; b[4 * P + c] = s.my;
+    b[5 * P + c] = s.Ch; b[6 * P + c] = s.Cl;
+}
+
+// Knuth's TwoSum: s + e == a + b exactly.
+template <class R>
+__device__ __forceinline__ void two_sum(R a, R b, R& s, R& e) {
+    s = a + b;
+    R bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+template <class R>
+__device__ __forceinline__ R clamp01(R c) { return c < R(0) ? R(0) : (c > R(1) ? R(1) : c); }
+
+// Quotient in the working precision: correctly rounded in FP64; in FP32 the
+// hardware approximate division (max error 2 ulp for |b| in [2^-126, 2^126]),
+// which is far inside the FP32 path's tolerance and much cheaper than the
+// IEEE division sequence.
+__device__ __forceinline__ double wdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float wdiv(float a, float b) { return __fdividef(a, b); }
+
+// Eq. 5-6 with the readings of the oracle: uniform latent heat, Eq. 7 mixture
+// heat capacity gated by clamp(C).  H = Hh + Hl (Hl = 0 in FP64); the
+// differences H - H_s and H - H_l are formed from the pair without rounding H.
+template <class R>
+__device__ __forceinline__ void invert_enthalpy(const Consts<R>& K, R Hh, R Hl, R Ct, R& T, R& Fl) {
+    const R cps = Ct * K.cp[0] + (R(1) - Ct) * K.cp[2];
+    const R cpl = Ct * K.cp[1] + (R(1) - Ct) * K.cp[2];
+    const R Hs = cps * K.Ts;
+    const R HL = cpl * K.Tl + K.L;
+    const R ds = (Hh - Hs) + Hl;
+    const R dl = (Hh - HL) + Hl;
+    if (ds < R(0)) {
+        Fl = R(0);
+        T = wdiv(Hh + Hl, cps);
+    } else if (dl > R(0)) {
+        Fl = R(1);
+        T = K.Tl + wdiv(dl, cpl);
+    } else if (HL > Hs) {
+        Fl = wdiv(ds, HL - Hs);
+        T = K.Ts + Fl * (K.Tl - K.Ts);
+    } else {
+        Fl = R(1);
+        T = K.Tl;
+    }
+}
+
+// Eq. 7 (reading R1): gamma = C~ [F_s g_s + F_l g_l] + (1 - C~) g_g.
+template <class R>
+__device__ __forceinline__ R mix(R Ct, R Fl, const R g[3]) {
+    return Ct * ((R(1) - Fl) * g[0] + Fl * g[1]) + (R(1) - Ct) * g[2];
+}
+
+// Map a cell coordinate outside [0, n) through its boundary: periodic wrap or
+// mirror about the wall (ghost layer k >= 1 mirrors interior cell k - 1).
+__device__ __forceinline__ void map_axis(int g, int n, int per, int lo_side, int& s, int& k, int& side) {
+    k = 0;
+    side = lo_side;
+    if (g >= 0 && g < n) { s = g; return; }
+    if (per) { s = ((g % n) + n) % n; return; }
+    if (g < 0) { k = -g; s = k - 1; side = lo_side; }
+    else { k = g - n + 1; s = n - k; side = lo_side + 1; }
+    s = s < 0 ? 0 : (s >= n ? n - 1 : s);   // layers deeper than the domain are never used
+}
+
+// Ghost value rules (boundary conditions on macroscopic variables).
+template <class R>
+struct Prim { R T, Fl, cp, rho, lam, mu, p, u, v, C; };
+
+template <class R>
+__device__ __forceinline__ void apply_ghost(const Consts<R>& K, int side, int k, bool x_normal, Prim<R>& q) {
+    if (K.bc_t[side] == BC_DIRICHLET_T) q.T = R(2) * K.Tw[side] - q.T;
+    const int f = K.bc_f[side];
+    if (f == BC_OUTLET) q.p = -q.p;
+    R& un = x_normal ? q.u : q.v;
+    R& ut = x_normal ? q.v : q.u;
+    if (f == BC_NOSLIP) { un = -un; ut = -ut; }
+    else if (f == BC_SYMMETRY) { un = -un; }
+    if (K.bc_c[side] == BC_WETTING) q.C = q.C + R(2 * k - 1) * K.wet[side] * q.C * (R(1) - q.C);
+}
+
+template <class R>
+__device__ __forceinline__ Prim<R> derive(const Consts<R>& K, const SV<R>& w) {
+    Prim<R> q;
+    const R C = w.Ch + w.Cl;
+    const R Ct = clamp01(C);
+    invert_enthalpy(K, w.Hh, w.Hl, Ct, q.T, q.Fl);
+    q.cp = mix(Ct, q.Fl, K.cp);
+    q.rho = mix(Ct, q.Fl, K.rho);
+    q.lam = mix(Ct, q.Fl, K.lam);
+    q.mu = mix(Ct, q.Fl, K.mu);
+    const R r3 = wdiv(R(3), q.rho);     // 1 / (rho cs^2)
+    q.u = w.mx * r3;
+    q.v = w.my * r3;
+    q.p = w.p;
+    q.C = C;
+    return q;
+}
+
+template <class R>
+__device__ __forceinline__ double pair_value(R hi, R lo) { return (double)hi + (double)lo; }
+
+template <class R>
+__device__ __forceinline__ void put_pair(R& hi, R& lo, double x) {
+    hi = (R)x;
+    lo = (R)(x - (double)hi);
+}
+
+}  // namespace eulbfs

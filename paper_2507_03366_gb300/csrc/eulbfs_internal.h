@@ -6,7 +6,6 @@
 
 namespace eulbfs {
 
-constexpr int kTileX = 32;   // tile width in cells: one warp spans a tile row
 constexpr int kHalo = 3;     // C halo; every other field needs 2 (gradient ring + its neighbours)
 constexpr int kMaxDomains = 1 << 20;
 
@@ -17,8 +16,7 @@ enum { XLO = 0, XHI = 1, YLO = 2, YHI = 3 };
 // double; the kernels convert them to their working precision.
 struct DomainDesc {
     int nx, ny;
-    int tiles_x, tiles_y;
-    int tile0;               // first global tile index of this domain
+    int strips, segs;        // work items of this domain along x and y
     int per_x, per_y;        // periodic axes
     int bc_t[4], bc_f[4], bc_c[4];  // thermal, flow, phase kind per side
     int zero_solid_velocity;
@@ -38,25 +36,72 @@ struct DomainDesc {
     void* st[3];
     void* Fsp;               // F_s of the previous step
     void* dFs;               // (F_s^n - F_s^{n-1}) / dt of the current step
+    int* flag;               // bit 0: this domain produced a non-finite state
     long long plane;         // nx * ny
 };
 
+// Working-precision copy of a domain's constants.  Built on the host for the
+// stage kernel (one per domain, copied into shared memory per work item) and
+// on the device by the auxiliary kernels.
+template <class R>
+struct Consts {
+    R rho[3], mu[3], lam[3], cp[3];
+    R L, Ts, Tl, beta, kappa, Qg, tau_g, Cref, kv, gx, gy, dt;
+    R six_over_Cref, inv_dt;   // 6 / C_ref = 1 / (C_ref cs^2 dt_s), 1 / dt
+    R Tw[4], wet[4];
+    int nx, ny, per_x, per_y, zsv, pad_;
+    int bc_t[4], bc_f[4], bc_c[4];
+    long long plane;
+    void* st[3];
+    void* Fsp;
+    void* dFs;
+    int* flag;
+};
+
+template <class R>
+__host__ __device__ inline void fill_consts(const DomainDesc& d, Consts<R>& K) {
+    for (int k = 0; k < 3; ++k) {
+        K.rho[k] = (R)d.rho[k]; K.mu[k] = (R)d.mu[k]; K.lam[k] = (R)d.lam[k]; K.cp[k] = (R)d.cp[k];
+    }
+    K.L = (R)d.L; K.Ts = (R)d.Ts; K.Tl = (R)d.Tl; K.beta = (R)d.beta; K.kappa = (R)d.kappa;
+    K.Qg = (R)d.Qg; K.tau_g = (R)d.tau_g; K.Cref = (R)d.Cref; K.kv = (R)d.kv;
+    K.gx = (R)d.gx; K.gy = (R)d.gy; K.dt = (R)d.dt;
+    K.six_over_Cref = (R)(6.0 / d.Cref);
+    K.inv_dt = (R)(1.0 / d.dt);
+    for (int k = 0; k < 4; ++k) {
+        K.Tw[k] = (R)d.Tw[k]; K.wet[k] = (R)d.wet[k];
+        K.bc_t[k] = d.bc_t[k]; K.bc_f[k] = d.bc_f[k]; K.bc_c[k] = d.bc_c[k];
+    }
+    K.nx = d.nx; K.ny = d.ny; K.per_x = d.per_x; K.per_y = d.per_y;
+    K.zsv = d.zero_solid_velocity; K.pad_ = 0;
+    K.plane = d.plane;
+    for (int k = 0; k < 3; ++k) K.st[k] = d.st[k];
+    K.Fsp = d.Fsp;
+    K.dFs = d.dFs;
+    K.flag = d.flag;
+}
+
+// Stage kernel geometry: a work item is a strip segment of one domain,
+// kStripX interior columns wide and `seg` rows high, swept in chunks of
+// kChunk rows (one warp per row, so kChunk warps per CTA).
+constexpr int kStripX = 31;   // 31 cells -> 32 x-faces per row: one per lane
+constexpr int kChunk = 8;
+constexpr int kStageThreads = 32 * kChunk;
+
 struct StageLaunch {
-    const DomainDesc* descs;
-    const int* tile_domain;  // domain of each global tile
-    int ntiles;
+    const void* consts;      // Consts<R>[ndomains] in device memory
+    const int4* items;       // (domain, strip, segment, 0)
+    int nitems;
     int stage;               // 0, 1, 2
+    int seg;                 // segment height in rows (multiple of kChunk)
     int* flag;               // bit 0: non-finite state seen
 };
 
-// Tile heights compiled into the stage kernel.
-constexpr int kTileYChoices[3] = {4, 8, 16};
-
-// Launch one Runge-Kutta stage over every tile of the batch.
-cudaError_t launch_stage(int precision, int tile_y, const StageLaunch& a, int grid, cudaStream_t s);
+// Launch one Runge-Kutta stage over every work item of the batch.
+cudaError_t launch_stage(int precision, const StageLaunch& a, int grid, cudaStream_t s);
 // Resident CTAs per SM of the stage kernel (for sizing the persistent grid).
-int stage_blocks_per_sm(int precision, int tile_y);
-size_t stage_smem_bytes(int precision, int tile_y);
+int stage_blocks_per_sm(int precision);
+size_t stage_smem_bytes(int precision);
 
 // Initial state from primitive fields (device double arrays); *bad is set
 // to 1 if any input value is NaN or Inf.

@@ -1,0 +1,445 @@
+// stage.cu -- the hot path of libeulbfs (sm_103a): one SSP-RK3 stage (Eq. 58)
+// of the EULBFS explicit step over every domain of a batch.
+//
+// Work decomposition.  A work item is a strip segment of one domain: 31
+// interior columns wide, `seg` rows high.  A CTA of 8 warps sweeps its segment
+// upwards in chunks of 8 rows, keeping the derived fields of the rows it needs
+// in a 16-row ring buffer in shared memory, so every cell of the segment is
+// loaded and derived once per stage (plus a 3-column halo on each side and a
+// 6-row prologue per segment).  Per chunk:
+//   1. load and derive 8 new rows: stage state -> T, F_l, C_p, rho, lambda,
+//      mu (Eq. 5-7), u = m / (rho cs^2), p, C; halo cells outside the domain
+//      are mapped through the boundary rules (mirror + value rule, or wrap);
+//   2. mu_c = 2 beta C (C-1)(2C-1) - kappa lap C (Sec. 2.3.1) for 8 rows;
+//      a wall ghost takes the value at its mirror cell;
+//   3. every face once: warp w computes the 32 x-faces of chunk row w (one
+//      per lane: 31 cells have 32 x-faces) and the 31 y-faces below row w+1
+//      (the face row below the chunk comes from the previous chunk);
+//   4. per cell: R(W) = -div F + F_E (Eq. 51-52), the Runge-Kutta stage, the
+//      optional solid projection, a non-finite check, and the store.
+// Work items span all domains of the batch, so one launch advances every
+// domain by one stage; the grid is persistent and strides over the items.
+//
+// The face computation is written in the face frame (n, t): an x-face has
+// n = x, t = y and a y-face n = y, t = x (D2Q9 is symmetric under the swap).
+// With dt_s = 0.5 the surrounding points x_f - e_a dt_s of a face are the two
+// cell centres (e_n = +-1, e_t = 0), the two cells' extrapolations half a cell
+// along t (e_n = +-1, e_t = +-1) and three points on the face itself (e_n = 0),
+// which take the mean of the two one-sided reconstructions (Eq. 54, R7).
+#include "device_common.cuh"
+
+namespace eulbfs {
+
+namespace {
+
+constexpr int RW = kStripX + 2 * kHalo;   // ring columns: strip plus halo (37)
+constexpr int RING = 16;                  // ring rows (power of two)
+constexpr int NT = kStageThreads;         // 8 warps
+enum { F_T, F_FL, F_CP, F_RHO, F_LAM, F_MU, F_P, F_U, F_V, F_C, F_MUC, NF };
+constexpr int FS = RING * RW;             // field stride in the ring
+
+template <class R>
+struct Smem {
+    R P[NF][RING][RW];        // derived fields, ring of rows (row r in slot r & 15)
+    R YF[6][RING][32];        // y-face fluxes, ring of face rows
+    R XF[6][kChunk][32];      // x-face fluxes of the current chunk
+    Consts<R> K;
+};
+
+__device__ __forceinline__ int slot(int r) { return r & (RING - 1); }
+
+// Step 1: rows [r0, r0 + nrows) of the strip (all RW columns).
+template <class R>
+__device__ __forceinline__ void load_rows(Smem<R>& S, const R* in, int x0, int r0, int nrows) {
+    const Consts<R>& K = S.K;
+    const int total = nrows * RW;
+    for (int idx = threadIdx.x; idx < total; idx += NT) {
+        const int rr = idx / RW, cc = idx - rr * RW;
+        const int gy = r0 + rr, gx = x0 + cc - kHalo;
+        int sx, kx, sdx, sy, ky, sdy;
+        map_axis(gx, K.nx, K.per_x, XLO, sx, kx, sdx);
+        map_axis(gy, K.ny, K.per_y, YLO, sy, ky, sdy);
+        const SV<R> w = load_state(in, K.plane, (long long)sy * K.nx + sx);
+        Prim<R> q = derive(K, w);
+        if (kx) apply_ghost(K, sdx, kx, true, q);    // x sides first, then y (corners)
+        if (ky) apply_ghost(K, sdy, ky, false, q);
+        const int s = slot(gy);
+        S.P[F_T][s][cc] = q.T;
+        S.P[F_FL][s][cc] = q.Fl;
+        S.P[F_CP][s][cc] = q.cp;
+        S.P[F_RHO][s][cc] = q.rho;
+        S.P[F_LAM][s][cc] = q.lam;
+        S.P[F_MU][s][cc] = q.mu;
+        S.P[F_P][s][cc] = q.p;
+        S.P[F_U][s][cc] = q.u;
+        S.P[F_V][s][cc] = q.v;
+        S.P[F_C][s][cc] = q.C;
+    }
+}
+
+// Step 2: mu_c (reading R5, 5-point Laplacian) for rows [r0, r0 + nrows),
+// columns 1 .. RW-2.  A wall ghost (layer 1 or 2) evaluates the Laplacian at
+// its mirror cell, which equals mirroring the interior value; deeper layers
+// are never read by a face of the strip and get 0.
+template <class R>
+__device__ __forceinline__ void muc_rows(Smem<R>& S, int x0, int r0, int nrows) {
+    const Consts<R>& K = S.K;
+    constexpr int NC = RW - 2;
+    const int total = nrows * NC;
+    const R* C = &S.P[F_C][0][0];
+    for (int idx = threadIdx.x; idx < total; idx += NT) {
+        const int rr = idx / NC, cc = 1 + idx - rr * NC;
+        const int gy = r0 + rr, gx = x0 + cc - kHalo;
+        int mc = cc, my = gy, deep = 0;
+        if (!K.per_x) {
+            if (gx < 0) { const int k = -gx; mc = cc + 2 * k - 1; deep |= k > 2; }
+            else if (gx >= K.nx) { const int k = gx - K.nx + 1; mc = cc - (2 * k - 1); deep |= k > 2; }
+        }
+        if (!K.per_y) {
+            if (gy < 0) { const int k = -gy; my = gy + 2 * k - 1; deep |= k > 2; }
+            else if (gy >= K.ny) { const int k = gy - K.ny + 1; my = gy - (2 * k - 1); deep |= k > 2; }
+        }
+        R mu = R(0);
+        if (!deep) {
+            const int s0 = slot(my) * RW + mc;
+            const R c = C[s0];
+            const R lap = C[s0 + 1] + C[s0 - 1] + C[slot(my + 1) * RW + mc] + C[slot(my - 1) * RW + mc] - R(4) * c;
+            mu = R(2) * K.beta * c * (c - R(1)) * (R(2) * c - R(1)) - K.kappa * lap;
+        }
+        S.P[F_MUC][slot(gy)][cc] = mu;
+    }
+}
+
+// The 9 surrounding-point values of one field of a face (Eq. 54, R7), given
+// the ring offsets of the L and R cells, their outer n-neighbours and their
+// t-neighbours.
+struct FaceIdx { int L, R, LL, RR, Lp, Lm, Rp, Rm; };
+
+template <class R>
+__device__ __forceinline__ void points(const R* f, const FaceIdx& x, R o[9]) {
+    const R l = f[x.L], r = f[x.R];
+    const R lf = l + R(0.25) * (r - f[x.LL]);     // L reconstructed at the face (half-cell step)
+    const R rf = r - R(0.25) * (f[x.RR] - l);     // R reconstructed at the face
+    const R dtl = f[x.Lp] - f[x.Lm];              // 2 x t-gradient of L (central difference)
+    const R dtr = f[x.Rp] - f[x.Rm];
+    o[0] = R(0.5) * (lf + rf);
+    const R st = R(0.125) * (dtl + dtr);          // mean half-cell t-step of L and R
+    o[2] = o[0] - st;
+    o[4] = o[0] + st;
+    o[1] = l;
+    o[3] = r;
+    o[5] = l - R(0.25) * dtl;
+    o[8] = l + R(0.25) * dtl;
+    o[6] = r - R(0.25) * dtr;
+    o[7] = r + R(0.25) * dtr;
+}
+
+template <class R>
+__device__ __forceinline__ R point0(const R* f, const FaceIdx& x) {
+    const R l = f[x.L], r = f[x.R];
+    const R lf = l + R(0.25) * (r - f[x.LL]);
+    const R rf = r - R(0.25) * (f[x.RR] - l);
+    return R(0.5) * (lf + rf);
+}
+
+template <class R>
+struct FaceFlux { R Fh, Fp, Fmn, Fmt, Fc, un; };
+
+// Sec. 2.5 steps (2)-(4) and Eq. 53 for one face.  The face equilibria enter
+// only through their closed moments (C_p T u_n, cs^2 (p + rho u_n^2),
+// cs^2 rho u_n u_t, C u_n; Eq. 11 and the moments of Eq. 29, 42); the
+// surrounding equilibria are summed point by point.
+template <class R>
+__device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const R* P, const FaceIdx& x, int fUn, int fUt) {
+    R un[9], ut[9], pp[9], rr[9], TT[9], cp[9], CC[9], mc[9];
+    points(P + fUn * FS, x, un);
+    points(P + fUt * FS, x, ut);
+    points(P + F_P * FS, x, pp);
+    points(P + F_RHO * FS, x, rr);
+    points(P + F_T * FS, x, TT);
+    points(P + F_CP * FS, x, cp);
+    points(P + F_C * FS, x, CC);
+    points(P + F_MUC * FS, x, mc);
+    const R lamf = point0(P + F_LAM * FS, x);
+    const R muf = point0(P + F_MU * FS, x);
+    const R rho_f = rr[0];
+    const R w0 = R(4.0 / 9.0), w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
+
+    R pf = R(0), mn = R(0), mt = R(0), Cf = R(0);
+    R Sh = R(0), Sg = R(0), Snn_p = R(0), Snn_q = R(0), Snt_p = R(0), Snt_q = R(0);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const int en = (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
+        const int et = (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
+        const R w = a == 0 ? w0 : (a < 5 ? w1 : w5);
+        // e.u with the compile-time components of e (no multiply by 0 or +-1)
+        R eu;
+        if (en != 0 && et != 0) eu = (en > 0 ? un[a] : -un[a]) + (et > 0 ? ut[a] : -ut[a]);
+        else if (en != 0) eu = en > 0 ? un[a] : -un[a];
+        else if (et != 0) eu = et > 0 ? ut[a] : -ut[a];
+        else eu = R(0);
+        const R uu = un[a] * un[a] + ut[a] * ut[a];
+        // cs^2 (e.u/cs^2 + (e.u)^2/(2 cs^4) - u^2/(2 cs^2)) with cs^2 = 1/3
+        const R q = eu + R(1.5) * eu * eu - R(0.5) * uu;
+        const R f = w * (pp[a] + rr[a] * q);                       // Eq. 29
+        pf += f;
+        if (en != 0) mn += R(en) * f;
+        if (et != 0) mt += R(et) * f;
+        if (a == 0) {
+            Cf += CC[0] - R(3) * mc[0] * K.Qg * (R(1) - w0);        // Eq. 42, alpha = 0
+        } else {
+            const R g = R(3) * w * (mc[a] * K.Qg + CC[a] * eu);     // Eq. 42
+            Cf += g;
+            if (en != 0) {
+                Sg += R(en) * g;
+                const R h = w * (K.Cref * TT[a] + R(3) * (cp[a] * TT[a]) * q);   // Eq. 9
+                Sh += R(en) * h;
+                // Eq. 33 (reading R8): w (p + rho_f q), kept as its p and q parts
+                Snn_p += w * pp[a];
+                Snn_q += w * q;
+                if (et != 0) {
+                    Snt_p += R(en * et) * w * pp[a];
+                    Snt_q += R(en * et) * w * q;
+                }
+            }
+        }
+    }
+    // Eq. 56: rho_f cs^2 u_f = sum e f^eq; tau from the face properties (R9)
+    const R irf = wdiv(R(1), rho_f);
+    const R unf = R(3) * mn * irf, utf = R(3) * mt * irf;
+    const R th = K.six_over_Cref * lamf * irf;   // tau_h - 0.5 = lambda / (rho C_ref cs^2 dt_s)
+    const R tf = R(6) * muf * irf;               // tau_f - 0.5 = mu / (rho cs^2 dt_s)
+    const R tg = K.tau_g - R(0.5);
+    const R cs2 = R(1.0 / 3.0);
+    FaceFlux<R> F;
+    // h* = (1.5 - tau) h^eq(x_f) + (tau - 0.5) h^eq(x_f - e dt_s) (Eq. 13, 16)
+    F.Fh = (R(1) - th) * (cp[0] * TT[0]) * unf + th * Sh;
+    F.Fp = mn;                                    // sum e_n f^eq(x_f) = rho_f cs^2 u_n,f
+    // f* = (1.5 - tau_f) f^eq(x_f) + (tau_f - 0.5) f^eq-m (Eq. 35, 37 with R3)
+    F.Fmn = (R(1) - tf) * cs2 * (pf + rho_f * unf * unf) + tf * (Snn_p + rho_f * Snn_q);
+    F.Fmt = (R(1) - tf) * cs2 * rho_f * unf * utf + tf * (Snt_p + rho_f * Snt_q);
+    F.Fc = (R(1) - tg) * Cf * unf + tg * Sg;     // Eq. 44, 46
+    F.un = unf;
+    return F;
+}
+
+// Step 3, x-faces of ring row r: lane l computes the face between columns
+// l+2 and l+3 (cells x0+l-1 and x0+l).
+template <class R>
+__device__ __forceinline__ void x_face(Smem<R>& S, int r, int row_in_chunk, int lane) {
+    FaceIdx x;
+    const int cL = lane + 2;
+    x.L = slot(r) * RW + cL;
+    x.R = x.L + 1;
+    x.LL = x.L - 1;
+    x.RR = x.L + 2;
+    x.Lp = slot(r + 1) * RW + cL;
+    x.Lm = slot(r - 1) * RW + cL;
+    x.Rp = x.Lp + 1;
+    x.Rm = x.Lm + 1;
+    const FaceFlux<R> F = face_flux(S.K, &S.P[0][0][0], x, F_U, F_V);
+    S.XF[0][row_in_chunk][lane] = F.Fh;
+    S.XF[1][row_in_chunk][lane] = F.Fp;
+    S.XF[2][row_in_chunk][lane] = F.Fmn;   // x-momentum
+    S.XF[3][row_in_chunk][lane] = F.Fmt;   // y-momentum
+    S.XF[4][row_in_chunk][lane] = F.Fc;
+    S.XF[5][row_in_chunk][lane] = F.un;
+}
+
+// Step 3, y-faces of face row r (between rows r-1 and r), lane l < 31 at column l+3.
+template <class R>
+__device__ __forceinline__ void y_face(Smem<R>& S, int r, int lane) {
+    FaceIdx x;
+    const int c = lane + kHalo;
+    x.L = slot(r - 1) * RW + c;
+    x.R = slot(r) * RW + c;
+    x.LL = slot(r - 2) * RW + c;
+    x.RR = slot(r + 1) * RW + c;
+    x.Lp = x.L + 1;
+    x.Lm = x.L - 1;
+    x.Rp = x.R + 1;
+    x.Rm = x.R - 1;
+    const FaceFlux<R> F = face_flux(S.K, &S.P[0][0][0], x, F_V, F_U);
+    const int s = slot(r);
+    S.YF[0][s][lane] = F.Fh;
+    S.YF[1][s][lane] = F.Fp;
+    S.YF[2][s][lane] = F.Fmt;   // x-momentum
+    S.YF[3][s][lane] = F.Fmn;   // y-momentum
+    S.YF[4][s][lane] = F.Fc;
+    S.YF[5][s][lane] = F.un;
+}
+
+// Step 4 for the cell (r, x0 + lane).
+template <class R>
+__device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r, int row_in_chunk, int lane,
+                                            int* flag) {
+    const Consts<R>& K = S.K;
+    const int gx = x0 + lane;
+    const long long c = (long long)r * K.nx + gx;
+    const int q = slot(r) * RW + lane + kHalo;
+    const int qn = slot(r + 1) * RW + lane + kHalo, qs = slot(r - 1) * RW + lane + kHalo;
+    const int sr = slot(r), sn = slot(r + 1);
+    R Rk[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+        Rk[k] = -((S.XF[k][row_in_chunk][lane + 1] - S.XF[k][row_in_chunk][lane]) + (S.YF[k][sn][lane] - S.YF[k][sr][lane]));
+    const R divu = (S.XF[5][row_in_chunk][lane + 1] - S.XF[5][row_in_chunk][lane]) + (S.YF[5][sn][lane] - S.YF[5][sr][lane]);
+
+    const R* P = &S.P[0][0][0];
+    const R T = P[F_T * FS + q], Fl = P[F_FL * FS + q], Cp = P[F_CP * FS + q];
+    const R rho = P[F_RHO * FS + q], u = P[F_U * FS + q], v = P[F_V * FS + q], C = P[F_C * FS + q];
+    const R drx = R(0.5) * (P[F_RHO * FS + q + 1] - P[F_RHO * FS + q - 1]);
+    const R dry = R(0.5) * (P[F_RHO * FS + qn] - P[F_RHO * FS + qs]);
+    const R dmx = R(0.5) * (P[F_MUC * FS + q + 1] - P[F_MUC * FS + q - 1]);
+    const R dmy = R(0.5) * (P[F_MUC * FS + qn] - P[F_MUC * FS + qs]);
+    R dfs;
+    if (stage == 0) {   // reading R14: lagged dF_s/dt, fixed over the step
+        R* Fsp = reinterpret_cast<R*>(K.Fsp);
+        const R Fs = R(1) - Fl;
+        dfs = (Fs - Fsp[c]) * K.inv_dt;
+        reinterpret_cast<R*>(K.dFs)[c] = dfs;
+        Fsp[c] = Fs;
+    } else {
+        dfs = reinterpret_cast<const R*>(K.dFs)[c];
+    }
+    const R cs2 = R(1.0 / 3.0);
+    const R D = clamp01(C) * dfs;
+    Rk[0] += Cp * T * divu;                                           // Eq. 51 row 1
+    Rk[1] += u * (drx * cs2) + v * (dry * cs2) + rho * cs2 * K.kv * D;   // row 2
+    Rk[2] += cs2 * (-Fl * C * dmx + rho * K.gx - rho * u * D);         // row 3 (R13)
+    Rk[3] += cs2 * (-Fl * C * dmy + rho * K.gy - rho * v * D);         // row 4
+    Rk[4] += C * K.kv * D;                                             // row 5 (R12)
+
+    const R* in = reinterpret_cast<const R*>(K.st[stage]);
+    const SV<R> ws = load_state(in, K.plane, c);
+    const SV<R> wn = load_state(reinterpret_cast<const R*>(K.st[0]), K.plane, c);
+    SV<R> o;
+    if constexpr (sizeof(R) == 8) {
+        // Eq. 58 as written
+        const R A = stage == 0 ? R(1) : (stage == 1 ? R(0.75) : R(1.0 / 3.0));
+        const R B = stage == 0 ? R(0) : (stage == 1 ? R(0.25) : R(2.0 / 3.0));
+        const R Cd = (stage == 0 ? R(1) : (stage == 1 ? R(0.25) : R(2.0 / 3.0))) * K.dt;
+        o.Hh = A * wn.Hh + B * ws.Hh + Cd * Rk[0];
+        o.p = A * wn.p + B * ws.p + Cd * Rk[1];
+        o.mx = A * wn.mx + B * ws.mx + Cd * Rk[2];
+        o.my = A * wn.my + B * ws.my + Cd * Rk[3];
+        o.Ch = A * wn.Ch + B * ws.Ch + Cd * Rk[4];
+        o.Hl = R(0);
+        o.Cl = R(0);
+    } else {
+        // Eq. 58 as W^n + increment; H and C kept as compensated pairs.  TwoSum
+        // for the sum and the renormalisation keeps every pair canonical.
+        const R B = stage == 0 ? R(0) : (stage == 1 ? R(0.25) : R(2.0 / 3.0));
+        const R Cd = (stage == 0 ? R(1) : (stage == 1 ? R(0.25) : R(2.0 / 3.0))) * K.dt;
+        const R dH = B * ((ws.Hh - wn.Hh) + (ws.Hl - wn.Hl)) + Cd * Rk[0];
+        const R dC = B * ((ws.Ch - wn.Ch) + (ws.Cl - wn.Cl)) + Cd * Rk[4];
+        R s1, e1;
+        two_sum(wn.Hh, dH, s1, e1);
+        two_sum(s1, wn.Hl + e1, o.Hh, o.Hl);
+        two_sum(wn.Ch, dC, s1, e1);
+        two_sum(s1, wn.Cl + e1, o.Ch, o.Cl);
+        o.p = wn.p + (B * (ws.p - wn.p) + Cd * Rk[1]);
+        o.mx = wn.mx + (B * (ws.mx - wn.mx) + Cd * Rk[2]);
+        o.my = wn.my + (B * (ws.my - wn.my) + Cd * Rk[3]);
+    }
+    if (K.zsv) {   // reading R15: no motion of the solid part
+        R Tn, Fln;
+        const R Cn = o.Ch + o.Cl;
+        invert_enthalpy(K, o.Hh, o.Hl, clamp01(Cn), Tn, Fln);
+        const R keep = R(1) - clamp01(Cn) * (R(1) - Fln);
+        o.mx *= keep;
+        o.my *= keep;
+    }
+    if (!(isfinite(o.Hh) && isfinite(o.p) && isfinite(o.mx) && isfinite(o.my) && isfinite(o.Ch))) {
+        atomicOr(flag, 1);      // solver-wide
+        atomicOr(K.flag, 1);    // this domain
+    }
+    store_state(reinterpret_cast<R*>(K.st[stage == 2 ? 0 : stage + 1]), K.plane, c, o);
+}
+
+}  // namespace
+
+template <class R>
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) stage_kernel(StageLaunch a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<R>& S = *reinterpret_cast<Smem<R>*>(smem_raw);
+    __shared__ int cur_domain;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) cur_domain = -1;
+    __syncthreads();
+    const Consts<R>* consts = static_cast<const Consts<R>*>(a.consts);
+
+    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+        const int4 item = a.items[it];
+        const int prev = cur_domain;   // read by every thread before the barrier below
+        __syncthreads();               // the previous item is done with shared memory
+        if (item.x != prev) {
+            const unsigned* src = reinterpret_cast<const unsigned*>(consts + item.x);
+            unsigned* dst = reinterpret_cast<unsigned*>(&S.K);
+            for (int k = tid; k < (int)(sizeof(Consts<R>) / 4); k += NT) dst[k] = src[k];
+            if (tid == 0) cur_domain = item.x;
+            __syncthreads();
+        }
+        const int x0 = item.y * kStripX;
+        const int y0 = item.z * a.seg;
+        const int y1 = min(y0 + a.seg, S.K.ny);
+        const R* in = reinterpret_cast<const R*>(S.K.st[a.stage]);
+
+        // prologue: rows y0-3 .. y0+2, mu_c of rows y0-2 .. y0+1, y-face row y0
+        load_rows(S, in, x0, y0 - kHalo, 2 * kHalo);
+        __syncthreads();
+        muc_rows(S, x0, y0 - 2, 4);
+        __syncthreads();
+        if (warp == 0 && lane < kStripX) y_face(S, y0, lane);
+        // (the first chunk writes other ring rows: no barrier needed here)
+
+        for (int j0 = y0; j0 < y1; j0 += kChunk) {
+            load_rows(S, in, x0, j0 + kHalo, kChunk);     // rows j0+3 .. j0+10
+            __syncthreads();
+            muc_rows(S, x0, j0 + 2, kChunk);              // rows j0+2 .. j0+9
+            __syncthreads();
+            // one face at a time per thread (x then y) keeps register use low
+#pragma unroll 1
+            for (int k = 0; k < 2; ++k) {
+                if (k == 0) x_face(S, j0 + warp, warp, lane);
+                else if (lane < kStripX) y_face(S, j0 + 1 + warp, lane);
+            }
+            __syncthreads();
+            const int r = j0 + warp;
+            if (r < y1 && lane < kStripX && x0 + lane < S.K.nx) cell_update(S, a.stage, x0, r, warp, lane, a.flag);
+            __syncthreads();
+        }
+    }
+}
+
+template <class R>
+static cudaError_t launch_t(const StageLaunch& a, int grid, cudaStream_t s) {
+    const size_t smem = sizeof(Smem<R>);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    stage_kernel<R><<<grid, NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class R>
+static int blocks_per_sm_t() {
+    const size_t smem = sizeof(Smem<R>);
+    cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage_kernel<R>, NT, smem) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_stage(int precision, const StageLaunch& a, int grid, cudaStream_t s) {
+    return precision == 0 ? launch_t<double>(a, grid, s) : launch_t<float>(a, grid, s);
+}
+
+int stage_blocks_per_sm(int precision) { return precision == 0 ? blocks_per_sm_t<double>() : blocks_per_sm_t<float>(); }
+
+size_t stage_smem_bytes(int precision) { return precision == 0 ? sizeof(Smem<double>) : sizeof(Smem<float>); }
+
+}  // namespace eulbfs

@@ -105,6 +105,7 @@ SIGNATURES = [
     ("eulbfs_diagnostics", ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(Diag)]),
     ("eulbfs_launches_per_step", ct.c_int, [ct.c_void_p]),
     ("eulbfs_use_graphs", ct.c_int, [ct.c_void_p, ct.c_int]),
+    ("eulbfs_autotune", ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_float)]),
     ("eulbfs_set_tile", ct.c_int, [ct.c_void_p, ct.c_int]),
     ("eulbfs_diagnostics_noalloc", ct.c_int, [ct.c_int, ct.c_void_p, ct.c_int, ct.c_int, ct.POINTER(Props),
                                               ct.c_void_p, ct.c_void_p]),
@@ -220,6 +221,12 @@ class Solver:
 
     def set_tile(self, tile_y: int):
         _check(lib().eulbfs_set_tile(self._h, tile_y))
+
+    def autotune(self, steps_per_candidate: int = 10):
+        """Time the work-item heights on the live batch; returns (rows, ms per step)."""
+        rows, ms = ct.c_int(), ct.c_float()
+        _check(lib().eulbfs_autotune(self._h, steps_per_candidate, ct.byref(rows), ct.byref(ms)))
+        return rows.value, ms.value
 
     def launches_per_step(self) -> int:
         return lib().eulbfs_launches_per_step(self._h)

@@ -55,8 +55,9 @@ def test_no_cpu_fallback_without_gpu(lib):
 
 def test_invalid_arguments_rejected_before_device_work(lib):
     h = ct.c_void_p()
-    # null domain list
-    assert lib.eulbfs_batch_create(0, None, eulbfs.FP32C, None, ct.byref(h)) == eulbfs.EINVAL
+    # negative domain count, and a non-empty batch without a domain list
+    assert lib.eulbfs_batch_create(-1, None, eulbfs.FP32C, None, ct.byref(h)) == eulbfs.EINVAL
+    assert lib.eulbfs_batch_create(2, None, eulbfs.FP32C, None, ct.byref(h)) == eulbfs.EINVAL
     # tau_g <= 0.5 is invalid (Sec. 2.3.2: M_c = (tau_g - 0.5) Q_g dt_s)
     case = wl.conductive(32, 2)
     case.props.tau_g = 0.5

@@ -220,11 +220,11 @@ def test_state_round_trip_through_doubles(precision):
 
 
 @pytest.mark.parametrize("precision", [eulbfs.FP64, eulbfs.FP32C])
-def test_graph_replay_and_tile_shapes_bitwise(precision):
+def test_graph_replay_and_work_item_shapes_bitwise(precision):
     cases = wl.static_droplet_batch(3, sides=(40, 72))
     ref = eulbfs.Solver(cases, precision=precision)
     ref.step(12)
-    for tile in (4, 8, 16):
+    for tile in (8, 24, 64):
         s = eulbfs.Solver(cases, precision=precision)
         s.set_tile(tile)
         s.use_graphs(4)
