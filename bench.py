@@ -327,7 +327,7 @@ def main():
         serving_out = rep.summary()
         serving_out["arrival_rate_hz"] = 20.0
         serving_out["workload"] = ("droplet impact on a cold plate, sides U[256,1024]/32, We U[10,200], "
-                                   "Re U[100,2000], St U[0.05,0.5], end time t U/D = 0.02")
+                                   "Re U[100,2000], St U[0.05,0.5], drop released 0.1 side above the plate, end time t U/D = 0.015")
         if fp64:
             serving_out["fp64_sequential_s_est"] = rep.cell_steps / (fp64["value"] * 1e9)
 

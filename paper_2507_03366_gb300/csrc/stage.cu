@@ -116,95 +116,148 @@ __device__ __forceinline__ void muc_rows(Smem<R>& S, int x0, int r0, int nrows) 
 struct FaceIdx { int L, R, LL, RR, Lp, Lm, Rp, Rm; };
 
 template <class R>
-__device__ __forceinline__ void points(const R* f, const FaceIdx& x, R o[9]) {
-    const R l = f[x.L], r = f[x.R];
-    const R lf = l + R(0.25) * (r - f[x.LL]);     // L reconstructed at the face (half-cell step)
-    const R rf = r - R(0.25) * (f[x.RR] - l);     // R reconstructed at the face
-    const R dtl = f[x.Lp] - f[x.Lm];              // 2 x t-gradient of L (central difference)
-    const R dtr = f[x.Rp] - f[x.Rm];
-    o[0] = R(0.5) * (lf + rf);
-    const R st = R(0.125) * (dtl + dtr);          // mean half-cell t-step of L and R
-    o[2] = o[0] - st;
-    o[4] = o[0] + st;
-    o[1] = l;
-    o[3] = r;
-    o[5] = l - R(0.25) * dtl;
-    o[8] = l + R(0.25) * dtl;
-    o[6] = r - R(0.25) * dtr;
-    o[7] = r + R(0.25) * dtr;
+struct FaceFlux { R Fh, Fp, Fmn, Fmt, Fc, un; };
+
+// Reconstruction pieces of one field: the cell values l, r, the face value
+// o0 (mean of the two one-sided reconstructions) and the central
+// t-differences dtl, dtr of the two cells (half-cell t-step = dt / 4).
+template <class R>
+struct Rec { R l, r, o0, dtl, dtr; };
+
+template <class R>
+__device__ __forceinline__ Rec<R> rec(const R* f, const FaceIdx& x) {
+    Rec<R> z;
+    z.l = f[x.L];
+    z.r = f[x.R];
+    const R lf = z.l + R(0.25) * (z.r - f[x.LL]);
+    const R rf = z.r - R(0.25) * (f[x.RR] - z.l);
+    z.o0 = R(0.5) * (lf + rf);
+    z.dtl = f[x.Lp] - f[x.Lm];
+    z.dtr = f[x.Rp] - f[x.Rm];
+    return z;
+}
+
+// Values at the 9 points in the order 0..8 of the face frame:
+// 1, 3 cell centres; 5, 8 and 6, 7 the t-extrapolations of L and R;
+// 0 the face value; 2, 4 the face value shifted by the mean t-step.
+template <class R>
+__device__ __forceinline__ void all_points(const Rec<R>& z, R o[9]) {
+    const R st = R(0.125) * (z.dtl + z.dtr);
+    o[0] = z.o0;
+    o[1] = z.l;
+    o[2] = z.o0 - st;
+    o[3] = z.r;
+    o[4] = z.o0 + st;
+    o[5] = z.l - R(0.25) * z.dtl;
+    o[6] = z.r - R(0.25) * z.dtr;
+    o[7] = z.r + R(0.25) * z.dtr;
+    o[8] = z.l + R(0.25) * z.dtl;
 }
 
 template <class R>
-__device__ __forceinline__ R point0(const R* f, const FaceIdx& x) {
+__device__ __forceinline__ R face_value(const R* f, const FaceIdx& x) {
     const R l = f[x.L], r = f[x.R];
     const R lf = l + R(0.25) * (r - f[x.LL]);
     const R rf = r - R(0.25) * (f[x.RR] - l);
     return R(0.5) * (lf + rf);
 }
 
-template <class R>
-struct FaceFlux { R Fh, Fp, Fmn, Fmt, Fc, un; };
-
-// Sec. 2.5 steps (2)-(4) and Eq. 53 for one face.  The face equilibria enter
-// only through their closed moments (C_p T u_n, cs^2 (p + rho u_n^2),
-// cs^2 rho u_n u_t, C u_n; Eq. 11 and the moments of Eq. 29, 42); the
-// surrounding equilibria are summed point by point.
+// Sec. 2.5 steps (2)-(4) and Eq. 53 for one face.
+//
+// The face equilibria enter only through their closed moments (C_p T u_n,
+// cs^2 (p + rho u_n^2), cs^2 rho u_n u_t, C u_n; Eq. 11 and the moments of
+// Eq. 29, 42).  The sums over the surrounding points x_f - e_a dt_s are
+// split into their parts linear in one reconstructed field, which have
+// closed forms because the reconstruction is linear (the t-offsets cancel in
+// pairs):
+//   sum w p = 2/3 p_0 + (p_L + p_R)/6          sum e_n w p = (p_L - p_R)/6
+//   sum e_t w p = -(dp_L + dp_R)/24             sum e_n e_t w p = (dp_R - dp_L)/72
+//   sum_{e_n != 0} w p = (p_L + p_R)/6
+//   mu_c part of sum g = Q ((mu_L + mu_R)/2 - mu_0), of sum e_n g = Q (mu_L - mu_R)/2
+//   C_ref T part of sum e_n h = C_ref (T_L - T_R)/6
+// (dp = central t-difference), and the nonlinear parts (rho q, C e.u,
+// C_p T q, q) are summed point by point with one multiply per weight class.
 template <class R>
 __device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const R* P, const FaceIdx& x, int fUn, int fUt) {
-    R un[9], ut[9], pp[9], rr[9], TT[9], cp[9], CC[9], mc[9];
-    points(P + fUn * FS, x, un);
-    points(P + fUt * FS, x, ut);
-    points(P + F_P * FS, x, pp);
-    points(P + F_RHO * FS, x, rr);
-    points(P + F_T * FS, x, TT);
-    points(P + F_CP * FS, x, cp);
-    points(P + F_C * FS, x, CC);
-    points(P + F_MUC * FS, x, mc);
-    const R lamf = point0(P + F_LAM * FS, x);
-    const R muf = point0(P + F_MU * FS, x);
-    const R rho_f = rr[0];
-    const R w0 = R(4.0 / 9.0), w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
+    R un[9], ut[9], rr[9], CC[9];
+    all_points(rec(P + fUn * FS, x), un);
+    all_points(rec(P + fUt * FS, x), ut);
+    all_points(rec(P + F_RHO * FS, x), rr);
+    all_points(rec(P + F_C * FS, x), CC);
+    const Rec<R> T = rec(P + F_T * FS, x);
+    const Rec<R> cp = rec(P + F_CP * FS, x);
+    const Rec<R> p = rec(P + F_P * FS, x);
+    const R mu_l = P[F_MUC * FS + x.L], mu_r = P[F_MUC * FS + x.R];
+    const R mu_0 = face_value(P + F_MUC * FS, x);
+    const R lamf = face_value(P + F_LAM * FS, x);
+    const R muf = face_value(P + F_MU * FS, x);
 
-    R pf = R(0), mn = R(0), mt = R(0), Cf = R(0);
-    R Sh = R(0), Sg = R(0), Snn_p = R(0), Snn_q = R(0), Snt_p = R(0), Snt_q = R(0);
+    // side-point temperatures and heat capacities (e_n != 0 points only)
+    const R Ts[9] = {T.o0, T.l, R(0), T.r, R(0), T.l - R(0.25) * T.dtl, T.r - R(0.25) * T.dtr,
+                     T.r + R(0.25) * T.dtr, T.l + R(0.25) * T.dtl};
+    const R cs[9] = {cp.o0, cp.l, R(0), cp.r, R(0), cp.l - R(0.25) * cp.dtl, cp.r - R(0.25) * cp.dtr,
+                     cp.r + R(0.25) * cp.dtr, cp.l + R(0.25) * cp.dtl};
+
+    // accumulators per weight class: axis points 1-4 (w = 1/9), diagonal 5-8 (w = 1/36)
+    R fq0 = R(0);                                  // rho q at point 0 (w = 4/9)
+    R pf_a = R(0), mn_a = R(0), mt_a = R(0), pf_d = R(0), mn_d = R(0), mt_d = R(0);
+    R qn_a = R(0), qn_d = R(0), qt_d = R(0);       // sums of q for the f^eq-m moments
+    R ce_a = R(0), ce_d = R(0), cen_a = R(0), cen_d = R(0);   // C e.u and e_n C e.u
+    R th_a = R(0), th_d = R(0);                    // e_n C_p T q
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
         const int en = (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
         const int et = (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
-        const R w = a == 0 ? w0 : (a < 5 ? w1 : w5);
-        // e.u with the compile-time components of e (no multiply by 0 or +-1)
-        R eu;
+        const bool diag = a >= 5;
+        R eu;                                      // e.u with compile-time components of e
         if (en != 0 && et != 0) eu = (en > 0 ? un[a] : -un[a]) + (et > 0 ? ut[a] : -ut[a]);
         else if (en != 0) eu = en > 0 ? un[a] : -un[a];
         else if (et != 0) eu = et > 0 ? ut[a] : -ut[a];
         else eu = R(0);
         const R uu = un[a] * un[a] + ut[a] * ut[a];
-        // cs^2 (e.u/cs^2 + (e.u)^2/(2 cs^4) - u^2/(2 cs^2)) with cs^2 = 1/3
-        const R q = eu + R(1.5) * eu * eu - R(0.5) * uu;
-        const R f = w * (pp[a] + rr[a] * q);                       // Eq. 29
-        pf += f;
-        if (en != 0) mn += R(en) * f;
-        if (et != 0) mt += R(et) * f;
+        // q = cs^2 (e.u/cs^2 + (e.u)^2/(2 cs^4) - u^2/(2 cs^2)) with cs^2 = 1/3
+        const R q = (a == 0) ? R(-0.5) * uu : eu + R(1.5) * eu * eu - R(0.5) * uu;
+        const R fq = rr[a] * q;                    // non-p part of f^eq / w (Eq. 29)
         if (a == 0) {
-            Cf += CC[0] - R(3) * mc[0] * K.Qg * (R(1) - w0);        // Eq. 42, alpha = 0
+            fq0 = fq;
+            continue;
+        }
+        const R ce = CC[a] * eu;                   // non-mu part of g^eq / (3 w) (Eq. 42)
+        if (!diag) {
+            pf_a += fq;
+            ce_a += ce;
+            if (en > 0) { mn_a += fq; cen_a += ce; qn_a += q; }
+            if (en < 0) { mn_a -= fq; cen_a -= ce; qn_a += q; }
+            if (et > 0) mt_a += fq;
+            if (et < 0) mt_a -= fq;
         } else {
-            const R g = R(3) * w * (mc[a] * K.Qg + CC[a] * eu);     // Eq. 42
-            Cf += g;
-            if (en != 0) {
-                Sg += R(en) * g;
-                const R h = w * (K.Cref * TT[a] + R(3) * (cp[a] * TT[a]) * q);   // Eq. 9
-                Sh += R(en) * h;
-                // Eq. 33 (reading R8): w (p + rho_f q), kept as its p and q parts
-                Snn_p += w * pp[a];
-                Snn_q += w * q;
-                if (et != 0) {
-                    Snt_p += R(en * et) * w * pp[a];
-                    Snt_q += R(en * et) * w * q;
-                }
-            }
+            pf_d += fq;
+            ce_d += ce;
+            if (en > 0) { mn_d += fq; cen_d += ce; } else { mn_d -= fq; cen_d -= ce; }
+            if (et > 0) mt_d += fq; else mt_d -= fq;
+            qn_d += q;
+            if (en * et > 0) qt_d += q; else qt_d -= q;
+        }
+        if (en != 0) {
+            const R thq = (cs[a] * Ts[a]) * q;     // C_p T q (Eq. 9 without C_ref T)
+            if (diag) { if (en > 0) th_d += thq; else th_d -= thq; }
+            else { if (en > 0) th_a += thq; else th_a -= thq; }
         }
     }
-    // Eq. 56: rho_f cs^2 u_f = sum e f^eq; tau from the face properties (R9)
+    const R w0 = R(4.0 / 9.0), w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
+    // Eq. 56 and the moments of the surrounding equilibria
+    const R pf = R(2.0 / 3.0) * p.o0 + R(1.0 / 6.0) * (p.l + p.r) + w0 * fq0 + w1 * pf_a + w5 * pf_d;
+    const R mn = R(1.0 / 6.0) * (p.l - p.r) + w1 * mn_a + w5 * mn_d;
+    const R mt = R(-1.0 / 24.0) * (p.dtl + p.dtr) + w1 * mt_a + w5 * mt_d;
+    const R Cf = CC[0] + K.Qg * (R(0.5) * (mu_l + mu_r) - mu_0) + R(1.0 / 3.0) * ce_a + R(1.0 / 12.0) * ce_d;
+    const R Sg = R(0.5) * K.Qg * (mu_l - mu_r) + R(1.0 / 3.0) * cen_a + R(1.0 / 12.0) * cen_d;
+    const R Sh = R(1.0 / 6.0) * K.Cref * (T.l - T.r) + R(1.0 / 3.0) * th_a + R(1.0 / 12.0) * th_d;
+    const R Snn_p = R(1.0 / 6.0) * (p.l + p.r);
+    const R Snt_p = R(1.0 / 72.0) * (p.dtr - p.dtl);
+    const R Snn_q = w1 * qn_a + w5 * qn_d;
+    const R Snt_q = w5 * qt_d;
+    // rho_f cs^2 u_f = sum e f^eq (Eq. 56); tau from the face properties (R9)
+    const R rho_f = rr[0];
     const R irf = wdiv(R(1), rho_f);
     const R unf = R(3) * mn * irf, utf = R(3) * mt * irf;
     const R th = K.six_over_Cref * lamf * irf;   // tau_h - 0.5 = lambda / (rho C_ref cs^2 dt_s)
@@ -213,7 +266,7 @@ __device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const R* P,
     const R cs2 = R(1.0 / 3.0);
     FaceFlux<R> F;
     // h* = (1.5 - tau) h^eq(x_f) + (tau - 0.5) h^eq(x_f - e dt_s) (Eq. 13, 16)
-    F.Fh = (R(1) - th) * (cp[0] * TT[0]) * unf + th * Sh;
+    F.Fh = (R(1) - th) * (cp.o0 * T.o0) * unf + th * Sh;
     F.Fp = mn;                                    // sum e_n f^eq(x_f) = rho_f cs^2 u_n,f
     // f* = (1.5 - tau_f) f^eq(x_f) + (tau_f - 0.5) f^eq-m (Eq. 35, 37 with R3)
     F.Fmn = (R(1) - tf) * cs2 * (pf + rho_f * unf * unf) + tf * (Snn_p + rho_f * Snn_q);
