@@ -32,6 +32,15 @@ import numpy as np  # noqa: E402
 
 BYTES_PER_CELL_STEP = {1: 244, 0: 352}    # algorithmic HBM bytes per cell per time step (FP32C, FP64)
 STAGES = 3
+# FP32 operations per cell per stage of the FP32C stage kernel (FFMA counted
+# as 2), from the ncu instruction counters of one capture; the formulation's
+# arithmetic, so it changes only when the face/cell algebra changes.
+FP32_FLOPS_PER_CELL_STAGE = 1100
+# DRAM bytes per cell per launch of the stage kernel (ncu, average of the 3
+# stages, 2.32 M-cell capture scaled by cells).
+DRAM_BYTES_PER_CELL_LAUNCH = 64.4
+# FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x SM clock.
+SMS, FP32_LANES_PER_SM = 152, 128
 
 
 def parse():
@@ -254,15 +263,24 @@ def main():
     launches = STAGES * args.steps
 
     # ---- roofline of the stage kernel (the only kernel in the region) --------
+    # Arithmetic intensity 1100 flop / 81.3 B = 13.5 flop/B is above the
+    # machine balance (80.5 TFLOP/s / 6.68 TB/s = 12 flop/B): FP32 ALU roof.
     peaks = measured_peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    clk_mhz = (peaks or {}).get("sm_max_mhz", 2070.0)
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12      # TFLOP/s
     per_launch_ms = ms / launches
     alg_bytes = BYTES_PER_CELL_STEP[1] / STAGES * cells
-    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "peak_source": "measured" if peaks else "fallback",
-                "kernel": "eulbfs::stage_kernel<float>",
-                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": per_launch_ms}
+    achieved_gbs = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    flops = FP32_FLOPS_PER_CELL_STAGE * cells
+    achieved_tf = flops / (per_launch_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / fp32_peak, "traffic": DRAM_BYTES_PER_CELL_LAUNCH * cells,
+                "peak_source": "unit counts x max SM clock (152 x 128 x 2 x %.0f MHz)" % clk_mhz,
+                "kernel": "eulbfs::stage_kernel<float>", "flops_per_launch": flops, "avg_launch_ms": per_launch_ms,
+                "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
+                        "peak_source": "measured" if peaks else "fallback",
+                        "algorithmic_bytes_per_launch": alg_bytes}}
 
     # ---- FP64 plain GPU step on the same workload ------------------------------
     fp64 = None

@@ -50,9 +50,33 @@ __device__ __forceinline__ int slot(int r) { return r & (RING - 1); }
 
 // Step 1: rows [r0, r0 + nrows) of the strip (all RW columns).
 template <class R>
+__device__ __forceinline__ void store_prim(Smem<R>& S, int s, int cc, const Prim<R>& q) {
+    S.P[F_T][s][cc] = q.T;
+    S.P[F_FL][s][cc] = q.Fl;
+    S.P[F_CP][s][cc] = q.cp;
+    S.P[F_RHO][s][cc] = q.rho;
+    S.P[F_LAM][s][cc] = q.lam;
+    S.P[F_MU][s][cc] = q.mu;
+    S.P[F_P][s][cc] = q.p;
+    S.P[F_U][s][cc] = q.u;
+    S.P[F_V][s][cc] = q.v;
+    S.P[F_C][s][cc] = q.C;
+}
+
+template <class R>
 __device__ __forceinline__ void load_rows(Smem<R>& S, const R* in, int x0, int r0, int nrows) {
     const Consts<R>& K = S.K;
     const int total = nrows * RW;
+    if (x0 >= kHalo && x0 + kStripX + kHalo <= K.nx && r0 >= 0 && r0 + nrows <= K.ny) {
+        // every cell of these rows is inside the domain: no boundary mapping
+        const long long base = (long long)r0 * K.nx + (x0 - kHalo);
+        for (int idx = threadIdx.x; idx < total; idx += NT) {
+            const int rr = idx / RW, cc = idx - rr * RW;
+            const SV<R> w = load_state(in, K.plane, base + (long long)rr * K.nx + cc);
+            store_prim(S, slot(r0 + rr), cc, derive(K, w));
+        }
+        return;
+    }
     for (int idx = threadIdx.x; idx < total; idx += NT) {
         const int rr = idx / RW, cc = idx - rr * RW;
         const int gy = r0 + rr, gx = x0 + cc - kHalo;
@@ -63,17 +87,7 @@ __device__ __forceinline__ void load_rows(Smem<R>& S, const R* in, int x0, int r
         Prim<R> q = derive(K, w);
         if (kx) apply_ghost(K, sdx, kx, true, q);    // x sides first, then y (corners)
         if (ky) apply_ghost(K, sdy, ky, false, q);
-        const int s = slot(gy);
-        S.P[F_T][s][cc] = q.T;
-        S.P[F_FL][s][cc] = q.Fl;
-        S.P[F_CP][s][cc] = q.cp;
-        S.P[F_RHO][s][cc] = q.rho;
-        S.P[F_LAM][s][cc] = q.lam;
-        S.P[F_MU][s][cc] = q.mu;
-        S.P[F_P][s][cc] = q.p;
-        S.P[F_U][s][cc] = q.u;
-        S.P[F_V][s][cc] = q.v;
-        S.P[F_C][s][cc] = q.C;
+        store_prim(S, slot(gy), cc, q);
     }
 }
 
@@ -87,6 +101,18 @@ __device__ __forceinline__ void muc_rows(Smem<R>& S, int x0, int r0, int nrows) 
     constexpr int NC = RW - 2;
     const int total = nrows * NC;
     const R* C = &S.P[F_C][0][0];
+    if (x0 >= kHalo - 1 && x0 + NC - (kHalo - 1) <= K.nx && r0 >= 0 && r0 + nrows <= K.ny) {
+        // no wall ghost among these cells: the Laplacian in place
+        for (int idx = threadIdx.x; idx < total; idx += NT) {
+            const int rr = idx / NC, cc = 1 + idx - rr * NC;
+            const int gy = r0 + rr;
+            const int s0 = slot(gy) * RW + cc;
+            const R c = C[s0];
+            const R lap = C[s0 + 1] + C[s0 - 1] + C[slot(gy + 1) * RW + cc] + C[slot(gy - 1) * RW + cc] - R(4) * c;
+            S.P[F_MUC][slot(gy)][cc] = R(2) * K.beta * c * (c - R(1)) * (R(2) * c - R(1)) - K.kappa * lap;
+        }
+        return;
+    }
     for (int idx = threadIdx.x; idx < total; idx += NT) {
         const int rr = idx / NC, cc = 1 + idx - rr * NC;
         const int gy = r0 + rr, gx = x0 + cc - kHalo;
