@@ -141,20 +141,8 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b)) / max(nb, 1e-30)
 
 
-@pytest.mark.parametrize("make,steps", [(lambda: wl.conductive(256, 4), 1000),
-                                        (lambda: wl.three_phase(1024, 4, St=0.1), 1000),
-                                        (lambda: wl.three_phase(1024, 4, St=1.0), 1000)],
-                         ids=["conductive", "three_phase_St0.1", "three_phase_St1"])
-def test_fp32c_within_tolerances(make, steps):
-    case = make()
-    gpu = eulbfs.Solver([case], precision=eulbfs.FP32C)
-    d0g = gpu.diag()
-    gpu.step(steps)
-    ref = oracle.OracleSolver(case)
-    d0r = ref.diag()
-    ref.step(steps)
-    g, r = gpu.fields(), ref.fields()
-    dg, dr = gpu.diag(), ref.diag()
+def check_fp32c(g, r, dg, dr, d0g, d0r):
+    """The tolerances stated for the FP32 form against the FP64 oracle."""
     assert rel_l2(g["T"], r["T"]) <= 1e-3
     assert rel_l2(g["C"], r["C"]) <= 1e-3
     if np.linalg.norm(r["u"]) > 0:
@@ -166,6 +154,41 @@ def test_fp32c_within_tolerances(make, steps):
     drift_g = dg["mass"] / d0g["mass"] - 1.0
     drift_r = dr["mass"] / d0r["mass"] - 1.0
     assert abs(drift_g - drift_r) <= 1e-6
+
+
+FP32C_CASES = [
+    ("conductive_256x4", lambda: wl.conductive(256, 4), 1000),
+    ("three_phase_1024x4_St0.1", lambda: wl.three_phase(1024, 4, St=0.1), 1000),
+    ("three_phase_1024x4_St1", lambda: wl.three_phase(1024, 4, St=1.0), 1000),
+    ("droplet_64_wet60", lambda: wl.droplet(64, theta_deg=60.0, St=0.2, Tw=-0.8), 1000),
+    ("film_crop_72x40", lambda: wl.film(256).crop(72, 40), 1000),
+]
+
+
+@pytest.mark.parametrize("name,make,steps", FP32C_CASES, ids=[c[0] for c in FP32C_CASES])
+def test_fp32c_within_tolerances(name, make, steps):
+    case = make()
+    gpu = eulbfs.Solver([case], precision=eulbfs.FP32C)
+    d0g = gpu.diag()
+    gpu.step(steps)
+    ref = oracle.OracleSolver(case)
+    d0r = ref.diag()
+    ref.step(steps)
+    check_fp32c(gpu.fields(), ref.fields(), gpu.diag(), ref.diag(), d0g, d0r)
+
+
+def test_fp32c_batch_domain_in_launch_configuration():
+    """A 128 x 128 domain advanced inside the full 64-domain FP32C batch (the
+    benchmark's launch configuration) against the oracle run on it alone."""
+    cases = wl.static_droplet_batch(64)
+    k = [c.nx for c in cases].index(128)
+    gpu = eulbfs.Solver(cases, precision=eulbfs.FP32C)
+    d0g = gpu.diag(k)
+    gpu.step(300)
+    ref = oracle.OracleSolver(cases[k])
+    d0r = ref.diag()
+    ref.step(300)
+    check_fp32c(gpu.fields(k), ref.fields(), gpu.diag(k), ref.diag(), d0g, d0r)
 
 
 # ---------------------------------------------------------------------------
