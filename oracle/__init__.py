@@ -62,7 +62,7 @@ class BC(ct.Structure):
 
 
 class Numerics(ct.Structure):
-    _fields_ = [("dt", ct.c_double), ("dt_stream", ct.c_double)]
+    _fields_ = [("dt", ct.c_double), ("dt_stream", ct.c_double), ("axisymmetric", ct.c_int)]
 
 
 _DP = ct.POINTER(ct.c_double)
@@ -173,7 +173,7 @@ class OracleSolver:
                       for k in ("T", "Fl", "C", "u", "v", "p")}
         init = Init(*[_ptr(self._keep[k]) for k in ("T", "Fl", "C", "u", "v", "p")])
         P, B = props_struct(case.props), bc_struct(case.bc)
-        N = Numerics(case.dt, case.dt_stream)
+        N = Numerics(case.dt, case.dt_stream, int(getattr(case, "axisymmetric", 0)))
         err = ct.create_string_buffer(256)
         h = lib().or_create(case.nx, case.ny, ct.byref(P), ct.byref(B), ct.byref(N), ct.byref(init), err)
         if not h:

@@ -12,7 +12,8 @@
  *   or_heq              Eq. 9        or_feq   Eq. 29
  *   or_feqm             Eq. 33-34 (R8)   or_geq Eq. 42
  *   face_flux           Sec. 2.5 steps (2)-(4): Eq. 54, 56, 13/16, 35/37, 44/46, 53
- *   residual            Eq. 51-52, 57
+ *   residual            Eq. 51-52, 57 (planar, or axisymmetric (r, z) with
+ *                       r-weighted volumes/areas and the hoop source)
  *   or_step             Eq. 58 and Sec. 2.5 steps (5)-(7)
  */
 #include "oracle.h"
@@ -250,8 +251,15 @@ static void compute_muc(or_solver* s) {
         for (int i = 0; i < s->nx; ++i) {
             const int q = PI(s, i, j);
             const double c = C[q];
-            const double lap = C[PI(s, i + 1, j)] + C[PI(s, i - 1, j)] + C[PI(s, i, j + 1)] +
-                               C[PI(s, i, j - 1)] - 4.0 * c;
+            double lap;
+            if (s->N.axisymmetric) {
+                /* (1/r) d/dr (r dC/dr) + d2C/dz2, faces at r = i and i + 1 */
+                const double rc = i + 0.5;
+                lap = (((i + 1.0) * (C[PI(s, i + 1, j)] - c) - i * (c - C[PI(s, i - 1, j)])) / rc) +
+                      (C[PI(s, i, j + 1)] + C[PI(s, i, j - 1)] - 2.0 * c);
+            } else {
+                lap = C[PI(s, i + 1, j)] + C[PI(s, i - 1, j)] + C[PI(s, i, j + 1)] + C[PI(s, i, j - 1)] - 4.0 * c;
+            }
             s->prim[P_MUC][q] = 2.0 * s->beta * c * (c - 1.0) * (2.0 * c - 1.0) - s->kappa * lap;
         }
     const int f = P_MUC;
@@ -330,6 +338,19 @@ static void face_flux(const or_solver* s, int dir, int i, int j, double out[6]) 
         feqms[a] = or_feqm(a, q[a][P_P], rho_f, q[a][P_U], q[a][P_V]);
         geqs[a] = or_geq(a, q[a][P_C], q[a][P_MUC], s->Qg, q[a][P_U], q[a][P_V]);
     }
+    if (s->N.axisymmetric && xf > 0.0) {
+        /* Axisymmetric runs (reading R24): the pressure equation has the
+         * extra source -rho cs^2 u_r / r, which the planar stencil does not
+         * see.  It is streamed with the surrounding distributions (weight
+         * w_alpha, over dt_s) so that p at the face is advanced with the full
+         * 3-D divergence; evaluated with the face values.  On the axis the
+         * face area is zero and nothing is added. */
+        const double Sp = -dts * rho_f * CS2 * q[0][P_U] / xf;
+        for (int a = 0; a < 9; ++a) {
+            feqs[a] += WA[a] * Sp;
+            feqms[a] += WA[a] * Sp;
+        }
+    }
 
     /* step (3): face macroscopic variables, Eq. 56 */
     double Hf = 0.0, pf = 0.0, mxf = 0.0, myf = 0.0, Cf = 0.0;
@@ -394,10 +415,17 @@ static void residual(or_solver* s, double* const W[5], double* const R[5]) {
             const double* fe = &s->fx[(j * (nx + 1) + i + 1) * 6];
             const double* fs = &s->fy[(j * nx + i) * 6];
             const double* fn = &s->fy[((j + 1) * nx + i) * 6];
-            /* Eq. 52 with V = S = 1: outward normals +x at fe, -x at fw, etc. */
-            double divF[5];
-            for (int k = 0; k < 5; ++k) divF[k] = (fe[k] - fw[k]) + (fn[k] - fs[k]);
-            const double divu = (fe[5] - fw[5]) + (fn[5] - fs[5]);   /* R6 */
+            /* Eq. 52: planar V = S = 1; axisymmetric (per radian) V = r_i,
+             * S = r_f on the radial faces and r_i on the axial faces. */
+            double divF[5], divu;
+            if (s->N.axisymmetric) {
+                const double rc = i + 0.5, rw = i, re = i + 1.0;
+                for (int k = 0; k < 5; ++k) divF[k] = (re * fe[k] - rw * fw[k]) / rc + (fn[k] - fs[k]);
+                divu = (re * fe[5] - rw * fw[5]) / rc + (fn[5] - fs[5]);
+            } else {
+                for (int k = 0; k < 5; ++k) divF[k] = (fe[k] - fw[k]) + (fn[k] - fs[k]);
+                divu = (fe[5] - fw[5]) + (fn[5] - fs[5]);   /* R6 */
+            }
 
             const double T = s->prim[P_T][q], Fl = s->prim[P_FL][q], Cp = s->prim[P_CP][q];
             const double rho = s->prim[P_RHO][q], u = s->prim[P_U][q], v = s->prim[P_V][q];
@@ -413,6 +441,11 @@ static void residual(or_solver* s, double* const W[5], double* const R[5]) {
             FE[2] = CS2 * (Fsx + rho * s->P.gx + Fix);
             FE[3] = CS2 * (Fsy + rho * s->P.gy + Fiy);
             FE[4] = C * kv * D;                                /* R12: Eq. 47 source */
+            if (s->N.axisymmetric) {
+                /* hoop stress of the radial momentum equation: + cs^2 (p - 2 mu u_r / r) / r */
+                const double rc = i + 0.5;
+                FE[2] += CS2 * (s->prim[P_P][q] - 2.0 * s->prim[P_MU][q] * u / rc) / rc;
+            }
             for (int k = 0; k < 5; ++k) R[k][c] = -divF[k] + FE[k];
         }
 }
@@ -477,6 +510,11 @@ or_solver* or_create(int nx, int ny, const or_props* P, const or_bc* B, const or
         return NULL;
     }
     if (!I || !I->T || !I->C) { bad(err, "initial T and C are required"); return NULL; }
+    if (N->axisymmetric && !(B->xlo.thermal == OR_BC_ADIABATIC && B->xlo.flow == OR_BC_SYMMETRY &&
+                             B->xlo.phase == OR_BC_NOFLUX)) {
+        bad(err, "axisymmetric runs need the axis x = 0 as an adiabatic, symmetric, no-flux side");
+        return NULL;
+    }
 
     or_solver* s = (or_solver*)calloc(1, sizeof(or_solver));
     s->nx = nx; s->ny = ny; s->px = nx + 2 * NG; s->py = ny + 2 * NG;
@@ -564,20 +602,22 @@ void or_diagnostics(const or_solver* s, or_diag* d) {
     d->t = s->t;
     for (int c = 0; c < n; ++c) {
         const double H = s->W[0][c], C = s->W[4][c];
+        const double w = s->N.axisymmetric ? (c % s->nx) + 0.5 : 1.0;   /* cell volume */
         for (int k = 0; k < 5; ++k)
             if (!isfinite(s->W[k][c])) d->nonfinite = 1;
         double T, Fl;
         or_invert_enthalpy(&s->P, H, C, &T, &Fl);
         const double rho = or_mix(&s->P, C, Fl, 0);
-        d->mass += rho;
-        d->enthalpy += H;
-        d->phase_vol += C;
-        d->solid_vol += clamp01(C) * (1.0 - Fl);
+        d->mass += w * rho;
+        d->enthalpy += w * H;
+        d->phase_vol += w * C;
+        d->solid_vol += w * clamp01(C) * (1.0 - Fl);
         const double sp = sqrt(s->W[2][c] * s->W[2][c] + s->W[3][c] * s->W[3][c]) / (rho * CS2);
         if (sp > d->max_speed) d->max_speed = sp;
     }
-    d->front_pos = d->solid_vol / s->ny;
-    d->interface_pos = d->phase_vol / s->ny;
+    const double base = s->N.axisymmetric ? 0.5 * (double)s->nx * s->nx : (double)s->ny;
+    d->front_pos = d->solid_vol / base;
+    d->interface_pos = d->phase_vol / base;
 }
 
 void or_get_state(const or_solver* s, double* H, double* p, double* mx, double* my, double* C,

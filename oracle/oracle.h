@@ -61,12 +61,15 @@ typedef struct { or_side xlo, xhi, ylo, yhi; } or_bc;
 typedef struct {
     double dt;        /* Runge-Kutta time step Delta t (Eq. 58) */
     double dt_stream; /* streaming step delta t (Sec. 2.5 step 1), 0 < dt_stream <= 0.5 */
+    int axisymmetric; /* 1: x is the radius r (axis at x = 0), y the axial coordinate z */
 } or_numerics;
 
 /* Initial primitive fields, host arrays of nx*ny doubles, copied at create.
  * Fl is the initial liquid fraction, used only where Ts <= T <= Tl. */
 typedef struct { const double *T, *Fl, *C, *u, *v, *p; } or_init;
 
+/* Integrals over the domain; in axisymmetric runs every cell is weighted by
+ * its radius r_i (volumes per radian). */
 typedef struct {
     long long step;
     double t;
@@ -74,8 +77,8 @@ typedef struct {
     double enthalpy;      /* sum of H */
     double phase_vol;     /* sum of C */
     double solid_vol;     /* sum of clamp(C)*F_s */
-    double front_pos;     /* solid_vol / ny */
-    double interface_pos; /* phase_vol / ny */
+    double front_pos;     /* solid_vol / (ny, or sum of r_i over a row) */
+    double interface_pos; /* phase_vol / (ny, or sum of r_i over a row) */
     double max_speed;     /* max |u| */
     int nonfinite;        /* 1 if any conserved value is NaN or Inf */
 } or_diag;

@@ -80,6 +80,7 @@ class Case:
     dt: float
     init: Dict[str, np.ndarray] = field(repr=False)
     dt_stream: float = 0.5
+    axisymmetric: int = 0      # 1: x is the radius r (axis at x = 0), y the axial z
 
     @property
     def cells(self) -> int:

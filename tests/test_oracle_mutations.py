@@ -14,6 +14,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "eulbfs_oracle.c")
 PINS = "tests/test_oracle_pins.py::"
+AXI = "tests/test_oracle_axisymmetric.py::"
 
 # (name, original text, planted text, pin that must fail)
 MUTATIONS = [
@@ -58,6 +59,23 @@ MUTATIONS = [
      "test_rigid_solid"),
     ("lagged_rate_R14", "s->dFs[c] = (Fs - s->Fsp[c]) / dt;", "s->dFs[c] = 0.5 * (Fs - s->Fsp[c]) / dt;",
      "test_freezing_momentum_decay"),
+    # axisymmetric form (reading R24 and the r-weighted balance of Eq. 52)
+    ("axi_planar_divergence", "for (int k = 0; k < 5; ++k) divF[k] = (re * fe[k] - rw * fw[k]) / rc + (fn[k] - fs[k]);",
+     "for (int k = 0; k < 5; ++k) divF[k] = (fe[k] - fw[k]) + (fn[k] - fs[k]);",
+     AXI + "test_cylinder_conduction_mode_decay"),
+    ("axi_hoop_pressure_dropped", "FE[2] += CS2 * (s->prim[P_P][q] - 2.0", "FE[2] += CS2 * (0.0 * s->prim[P_P][q] - 2.0",
+     AXI + "test_uniform_pressure_is_force_free"),
+    ("axi_hoop_viscous_dropped", "- 2.0 * s->prim[P_MU][q] * u / rc) / rc;", "- 0.0 * s->prim[P_MU][q] * u / rc) / rc;",
+     AXI + "test_stagnation_flow_residual_linear_part_vanishes"),
+    ("axi_streamed_source_R24", "const double Sp = -dts * rho_f * CS2 * q[0][P_U] / xf;", "const double Sp = 0.0;",
+     AXI + "test_stagnation_flow_residual_linear_part_vanishes"),
+    ("axi_planar_velocity_divergence", "divu = (re * fe[5] - rw * fw[5]) / rc + (fn[5] - fs[5]);",
+     "divu = (fe[5] - fw[5]) + (fn[5] - fs[5]);", AXI + "test_stagnation_flow_residual_linear_part_vanishes"),
+    ("axi_laplacian_face_radius", "lap = (((i + 1.0) * (C[PI(s, i + 1, j)] - c) - i * (c - C[PI(s, i - 1, j)])) / rc)",
+     "lap = (((i + 0.5) * (C[PI(s, i + 1, j)] - c) - (i + 0.5) * (c - C[PI(s, i - 1, j)])) / rc)",
+     AXI + "test_laplacian_of_r_squared"),
+    ("axi_volume_weight", "const double w = s->N.axisymmetric ? (c % s->nx) + 0.5 : 1.0;",
+     "const double w = s->N.axisymmetric ? (c % s->nx) + 1.0 : 1.0;", AXI + "test_sphere_volume_and_gibbs_thomson"),
 ]
 
 
@@ -71,6 +89,7 @@ def test_pin_catches_planted_mistake(name, orig, planted, pin, tmp_path):
     subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-fPIC", "-shared", "-D_DEFAULT_SOURCE",
                            "-I", os.path.join(ROOT, "oracle"), "-o", str(mut_so), str(mut_c), "-lm"])
     env = dict(os.environ, EULBFS_ORACLE_LIB=str(mut_so))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", PINS + pin],
+    node = pin if "::" in pin else PINS + pin
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", node],
                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pin {pin} passed on an oracle with '{name}' planted:\n{r.stdout[-2000:]}"
