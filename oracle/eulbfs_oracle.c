@@ -442,9 +442,12 @@ static void residual(or_solver* s, double* const W[5], double* const R[5]) {
             FE[3] = CS2 * (Fsy + rho * s->P.gy + Fiy);
             FE[4] = C * kv * D;                                /* R12: Eq. 47 source */
             if (s->N.axisymmetric) {
-                /* hoop stress of the radial momentum equation: + cs^2 (p - 2 mu u_r / r) / r */
+                /* hoop stress of the radial momentum equation, + Pi_thetatheta / r
+                 * (reading R24): the pressure advanced over dt_s like the face
+                 * pressures, p - dt_s div(rho cs^2 u), and the viscous -2 mu u_r / r */
                 const double rc = i + 0.5;
-                FE[2] += CS2 * (s->prim[P_P][q] - 2.0 * s->prim[P_MU][q] * u / rc) / rc;
+                FE[2] += CS2 * (s->prim[P_P][q] - s->N.dt_stream * divF[1] -
+                                2.0 * s->prim[P_MU][q] * u / rc) / rc;
             }
             for (int k = 0; k < 5; ++k) R[k][c] = -divF[k] + FE[k];
         }

@@ -12,6 +12,10 @@ for a cylinder or a body of revolution that the planar scheme gets wrong:
   * a fluid at rest under a uniform pressure feels no force;
   * the stagnation flow u = (a r, -2 a z) is divergence-free and free of
     viscous force, so the part of the residual linear in a vanishes;
+  * the uniform radial expansion u = (a r, 0) feels no force (its stresses
+    are uniform and isotropic in (r, theta)) and compresses at div u = 2a;
+  * a drop of revolution at rest in a gas 1000 times lighter stays at rest
+    (no mode of the linearised scheme grows);
   * heat conduction in a cylinder decays as J0(k r) exp(-alpha k^2 t) with
     k R = 2.4048 (the first zero of J0);
   * steady pipe flow is Hagen-Poiseuille, u_z = g (R^2 - r^2) / (4 nu);
@@ -105,6 +109,49 @@ def test_stagnation_flow_residual_linear_part_vanishes():
     inner = (slice(3, ny - 3), slice(0, nx - 3))     # away from the outlet ghosts
     for k in range(5):
         assert np.max(np.abs(lin[k][inner])) < 1e-8, k
+
+
+# ---------------------------------------------------------------------------
+# 3b. Uniform radial expansion u_r = a r, u_z = 0: div u = 2a, the viscous
+#     stress 2 mu a is the same in r and theta and the isotropic part of the
+#     face fluxes (the pressure advanced over dt_s) is uniform, so the
+#     radial momentum feels no force: its residual has no part linear in a.
+#     The pressure and phase equations compress at -rho cs^2 2a and -C 2a.
+# ---------------------------------------------------------------------------
+def test_uniform_radial_expansion():
+    nx, ny, a = 16, 4, 1e-6
+    P = _props(mu=(0.1,) * 3, Ts=-5.0, Tl=-5.0)
+    r = np.arange(nx) + 0.5
+    res = []
+    for sgn in (1.0, -1.0):
+        s = oracle.OracleSolver(_axi_case(nx, ny, P, wl.BC(AXIS, OUTLET, wl.PER, wl.PER), T=1.0, C=1.0,
+                                          u=np.broadcast_to(sgn * a * r, (ny, nx))))
+        res.append(s.residual())
+    lin = (res[0] - res[1]) / (2 * a)
+    inner = (slice(None), slice(0, nx - 3))
+    for k in (0, 2, 3):
+        assert np.max(np.abs(lin[k][inner])) < 1e-8, k
+    np.testing.assert_allclose(lin[1][inner], -2.0 * CS2, atol=1e-8)
+    np.testing.assert_allclose(lin[4][inner], -2.0, atol=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# 3c. A drop of revolution at rest in a gas 1000 times lighter (the impact
+#     problem's fluids) stays at rest up to the diffuse interface's small
+#     parasitic currents: no mode of the scheme grows near the axis.
+# ---------------------------------------------------------------------------
+def test_resting_drop_in_light_gas_stays_bounded():
+    side, R = 24, 6.0
+    P = wl.Props(wl.Phase(1.0, 0.0032, 0.05, 1.0), wl.Phase(1.0, 0.0032, 0.05, 1.0), wl.Phase(1e-3, 3.2e-5, 5e-5, 1.0),
+                 L=1.0, Ts=-5.0, Tl=-5.0, sigma=0.0016, xi=4.0, Mc=0.1, tau_g=1.0, gx=0.0, gy=0.0,
+                 zero_solid_velocity=0)
+    r = np.arange(side) + 0.5
+    z = np.arange(side) + 0.5 - side / 2
+    C = 0.5 * (1 + np.tanh(2 * (R - np.sqrt(r[None, :] ** 2 + z[:, None] ** 2)) / 4.0))
+    s = oracle.OracleSolver(_axi_case(side, side, P, wl.BC(AXIS, WALL, WALL, WALL), T=0.0, C=C))
+    for _ in range(8):
+        s.step(50)
+        assert s.diag()["max_speed"] < 0.01
 
 
 # ---------------------------------------------------------------------------

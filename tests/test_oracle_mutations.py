@@ -63,9 +63,14 @@ MUTATIONS = [
     ("axi_planar_divergence", "for (int k = 0; k < 5; ++k) divF[k] = (re * fe[k] - rw * fw[k]) / rc + (fn[k] - fs[k]);",
      "for (int k = 0; k < 5; ++k) divF[k] = (fe[k] - fw[k]) + (fn[k] - fs[k]);",
      AXI + "test_cylinder_conduction_mode_decay"),
-    ("axi_hoop_pressure_dropped", "FE[2] += CS2 * (s->prim[P_P][q] - 2.0", "FE[2] += CS2 * (0.0 * s->prim[P_P][q] - 2.0",
+    ("axi_hoop_pressure_dropped", "FE[2] += CS2 * (s->prim[P_P][q] - s->N.dt_stream",
+     "FE[2] += CS2 * (0.0 * s->prim[P_P][q] - s->N.dt_stream",
      AXI + "test_uniform_pressure_is_force_free"),
-    ("axi_hoop_viscous_dropped", "- 2.0 * s->prim[P_MU][q] * u / rc) / rc;", "- 0.0 * s->prim[P_MU][q] * u / rc) / rc;",
+    ("axi_hoop_pressure_not_advanced", "s->prim[P_P][q] - s->N.dt_stream * divF[1] -", "s->prim[P_P][q] -",
+     AXI + "test_uniform_radial_expansion"),
+    ("axi_hoop_pressure_not_advanced_stability", "s->prim[P_P][q] - s->N.dt_stream * divF[1] -", "s->prim[P_P][q] -",
+     AXI + "test_resting_drop_in_light_gas_stays_bounded"),
+    ("axi_hoop_viscous_dropped", "2.0 * s->prim[P_MU][q] * u / rc) / rc;", "0.0 * s->prim[P_MU][q] * u / rc) / rc;",
      AXI + "test_stagnation_flow_residual_linear_part_vanishes"),
     ("axi_streamed_source_R24", "const double Sp = -dts * rho_f * CS2 * q[0][P_U] / xf;", "const double Sp = 0.0;",
      AXI + "test_stagnation_flow_residual_linear_part_vanishes"),
