@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--serve", type=int, default=200, help="requests in the serving leg (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=4.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--geometry", default="rz", choices=["rz", "xy"],
+                    help="rz: axisymmetric (r, z) droplet domains; xy: planar 2-D")
     return ap.parse_args()
 
 
@@ -152,9 +154,9 @@ def measured_peaks():
         return None
 
 
-def workload(n_domains: int, seed: int):
+def workload(n_domains: int, seed: int, geometry: str = "rz"):
     from paper_2507_03366_gb300 import workloads as wl
-    return wl.static_droplet_batch(n_domains, seed=seed)
+    return wl.static_droplet_batch(n_domains, seed=seed, axisymmetric=geometry == "rz")
 
 
 def cpu_baseline(cases, seconds: float) -> dict:
@@ -180,7 +182,8 @@ METRIC = "GCUPS coupled EULBFS step, FP32 batched vs FP64 plain; p50/p99 solve l
 
 def workload_config(cases, world: int, args) -> dict:
     cells = sum(c.cells for c in cases)
-    return {"workload": f"static droplet freezing batch: {len(cases)} domains per GPU, sides "
+    geo = "axisymmetric (r, z)" if cases and cases[0].axisymmetric else "planar 2-D"
+    return {"workload": f"static droplet freezing batch, {geo}: {len(cases)} domains per GPU, sides "
                         f"{{128,192,256,384,512}}, {cells} cells per GPU",
             "global_batch": len(cases) * world, "seq_len": cells, "parallelism": f"independent domains x{world}",
             "precision": "FP32C", "work_item": f"31x{args.tile} strip segment", "graph_steps": args.graph,
@@ -193,7 +196,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    cases = workload(args.domains, rank_seed(args.seed, 0))
+    cases = workload(args.domains, rank_seed(args.seed, 0), args.geometry)
     import oracle
     case = min(cases, key=lambda c: c.cells)
     s = oracle.OracleSolver(case)
@@ -231,7 +234,7 @@ def main():
         torch.cuda.set_device(0)
     from paper_2507_03366_gb300 import eulbfs
 
-    cases = workload(args.domains, rank_seed(args.seed, rank))
+    cases = workload(args.domains, rank_seed(args.seed, rank), args.geometry)
     cells = sum(c.cells for c in cases)
     stream = torch.cuda.Stream()
     sol = eulbfs.Solver(cases, precision=eulbfs.FP32C, stream=stream.cuda_stream)
@@ -339,7 +342,7 @@ def main():
     if args.serve > 0:
         from paper_2507_03366_gb300 import serving
         from paper_2507_03366_gb300 import workloads as wl
-        reqs = wl.impact_requests(args.serve, seed=5 + 1000 * rank)
+        reqs = wl.impact_requests(args.serve, seed=5 + 1000 * rank, axisymmetric=args.geometry == "rz")
         rep = serving.serve(reqs, precision=eulbfs.FP32C, budget_bytes=int(args.serve_budget_gb * 2 ** 30),
                             chunk=16, stream=stream.cuda_stream, realtime=True)
         serving_out = rep.summary()

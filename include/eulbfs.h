@@ -82,6 +82,14 @@ typedef struct { eulbfs_side xlo, xhi, ylo, yhi; } eulbfs_bc;
 
 typedef struct {
     double dt;  /* Runge-Kutta time step Delta t (Eq. 58), chosen by the caller's CFL bound */
+    /* 0: planar 2-D.  1: axisymmetric (r, z): x is the radius r with the axis
+     * at x = 0 and y the axial coordinate.  The finite-volume balance (Eq. 52)
+     * then uses per-radian cell volumes r_i and face areas r_f (radial faces)
+     * or r_i (axial faces), adds the hoop term cs^2 (p - 2 mu u_r / r) / r to
+     * the radial momentum, takes the axisymmetric Laplacian in mu_c and the
+     * axisymmetric mass source -rho cs^2 u_r / r in the face pressure.  The
+     * xlo side must be ADIABATIC / SYMMETRY / NOFLUX (EINVAL otherwise). */
+    int axisymmetric;
 } eulbfs_numerics;
 
 /* Initial primitive fields: host arrays of nx*ny doubles, copied at creation.
@@ -102,16 +110,18 @@ typedef struct {
 typedef struct { double *H, *T, *Fl, *C, *p, *u, *v; } eulbfs_fields_out;
 
 /* Global diagnostics of one domain, accumulated in FP64 on the device
- * (fixed-order reduction, bitwise reproducible). */
+ * (fixed-order reduction, bitwise reproducible).  Sums are over cell volumes:
+ * 1 per cell in planar domains, r_i = i + 1/2 (per radian) in axisymmetric
+ * ones. */
 typedef struct {
     long long step;       /* completed time steps */
     double t;             /* simulated time = step * dt */
-    double mass;          /* sum of rho (cell volume 1) */
+    double mass;          /* sum of rho */
     double enthalpy;      /* sum of H */
     double phase_vol;     /* sum of C */
     double solid_vol;     /* sum of clamp(C,0,1) * F_s */
-    double front_pos;     /* solid_vol / ny: solid thickness per unit width */
-    double interface_pos; /* phase_vol / ny: condensed thickness per unit width */
+    double front_pos;     /* solid_vol / ny (axisymmetric: / (nx^2 / 2)): flat-front solid thickness */
+    double interface_pos; /* phase_vol / ny (axisymmetric: / (nx^2 / 2)): flat condensed thickness */
     double max_speed;     /* max |u| */
     int nonfinite;        /* 1 if any state value is NaN or Inf */
 } eulbfs_diag;
@@ -211,7 +221,9 @@ int eulbfs_set_tile(eulbfs_solver* s, int rows);
  * cannot let a library call cudaMalloc or cudaFree: programs whose device
  * memory is fully committed to another framework's allocator, and loops that
  * cannot afford cudaFree's device-wide synchronisation or a driver allocation
- * in the middle of a step.  It computes what eulbfs_diagnostics computes.
+ * in the middle of a step.  It computes what eulbfs_diagnostics computes
+ * for a planar domain (every cell volume 1; it is not told the geometry, so
+ * for an axisymmetric domain the sums are unweighted).
  *   state: device pointer to the conserved-state planes of one domain in the
  *          working precision, nx*ny values per plane, planes back to back:
  *          FP64 5 planes of doubles (H, p, rho cs^2 u, rho cs^2 v, C); FP32C

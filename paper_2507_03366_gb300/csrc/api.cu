@@ -88,6 +88,10 @@ int validate(const eulbfs_grid& g, const eulbfs_props& P, const eulbfs_bc& B, co
         return fail(EULBFS_EINVAL, "need L >= 0, Ts <= Tl, sigma >= 0, Mc >= 0, tau_g > 0.5");
     if (P.sigma > 0 && !(P.xi > 0)) return fail(EULBFS_EINVAL, "xi must be > 0 when sigma > 0");
     if (!(N.dt > 0 && std::isfinite(N.dt))) return fail(EULBFS_EINVAL, "dt must be > 0");
+    if (N.axisymmetric != 0 && N.axisymmetric != 1) return fail(EULBFS_EINVAL, "axisymmetric must be 0 or 1");
+    if (N.axisymmetric && !(B.xlo.thermal == EULBFS_BC_ADIABATIC && B.xlo.flow == EULBFS_BC_SYMMETRY &&
+                            B.xlo.phase == EULBFS_BC_NOFLUX))
+        return fail(EULBFS_EINVAL, "an axisymmetric domain needs the axis (xlo) adiabatic, symmetric and no-flux");
     return EULBFS_OK;
 }
 
@@ -106,6 +110,7 @@ DomainDesc make_desc(const eulbfs_grid& g, const eulbfs_props& P, const eulbfs_b
         d.wet[k] = (P.xi > 0) ? 4.0 * std::cos(sides[k]->theta_deg * M_PI / 180.0) / P.xi : 0.0;
     }
     d.zero_solid_velocity = P.zero_solid_velocity ? 1 : 0;
+    d.axi = N.axisymmetric ? 1 : 0;
     const eulbfs_phase* ph[3] = {&P.s, &P.l, &P.g};
     for (int k = 0; k < 3; ++k) {
         d.rho[k] = ph[k]->rho;
@@ -706,8 +711,11 @@ int eulbfs_diagnostics(eulbfs_solver* s, int slot, eulbfs_diag* out) {
     out->solid_vol = s->h_diag[3];
     out->max_speed = s->h_diag[4];
     out->nonfinite = s->h_diag[5] != 0.0 ? 1 : 0;
-    out->front_pos = out->solid_vol / d.grid.ny;
-    out->interface_pos = out->phase_vol / d.grid.ny;
+    // flat-front thickness: planar per unit width, axisymmetric over the
+    // cylinder's per-radian cross-section sum_i r_i = nx^2 / 2
+    const double base = d.desc.axi ? 0.5 * (double)d.grid.nx * d.grid.nx : (double)d.grid.ny;
+    out->front_pos = out->solid_vol / base;
+    out->interface_pos = out->phase_vol / base;
     if (out->nonfinite || bad) {
         out->nonfinite = 1;
         return fail(EULBFS_ENONFINITE, "domain state is not finite");

@@ -20,7 +20,7 @@ struct DomainDesc {
     int per_x, per_y;        // periodic axes
     int bc_t[4], bc_f[4], bc_c[4];  // thermal, flow, phase kind per side
     int zero_solid_velocity;
-    int pad_;
+    int axi;                 // 1: axisymmetric (r, z), x = r with the axis at x = 0
     double Tw[4];            // wall temperature per side (Dirichlet)
     double wet[4];           // 4 cos(theta) / xi per side (wetting)
     double rho[3], mu[3], lam[3], cp[3];   // solid, liquid, gas
@@ -49,7 +49,7 @@ struct Consts {
     R L, Ts, Tl, beta, kappa, Qg, tau_g, Cref, kv, gx, gy, dt;
     R six_over_Cref, inv_dt;   // 6 / C_ref = 1 / (C_ref cs^2 dt_s), 1 / dt
     R Tw[4], wet[4];
-    int nx, ny, per_x, per_y, zsv, pad_;
+    int nx, ny, per_x, per_y, zsv, axi;
     int bc_t[4], bc_f[4], bc_c[4];
     long long plane;
     void* st[3];
@@ -73,7 +73,7 @@ __host__ __device__ inline void fill_consts(const DomainDesc& d, Consts<R>& K) {
         K.bc_t[k] = d.bc_t[k]; K.bc_f[k] = d.bc_f[k]; K.bc_c[k] = d.bc_c[k];
     }
     K.nx = d.nx; K.ny = d.ny; K.per_x = d.per_x; K.per_y = d.per_y;
-    K.zsv = d.zero_solid_velocity; K.pad_ = 0;
+    K.zsv = d.zero_solid_velocity; K.axi = d.axi;
     K.plane = d.plane;
     for (int k = 0; k < 3; ++k) K.st[k] = d.st[k];
     K.Fsp = d.Fsp;

@@ -194,10 +194,12 @@ __global__ void __launch_bounds__(kDiagThreads) diag_partial_kernel(const Domain
         double T, Fl;
         invert_enthalpy(Kd, H, 0.0, clamp01(C), T, Fl);
         const double rho = mix(clamp01(C), Fl, Kd.rho);
-        acc[0] += rho;
-        acc[1] += H;
-        acc[2] += C;
-        acc[3] += clamp01(C) * (1.0 - Fl);
+        // cell volume: 1, or the radius r_i = i + 1/2 per radian (axisymmetric)
+        const double vol = Kd.axi ? (double)(c % Kd.nx) + 0.5 : 1.0;
+        acc[0] += vol * rho;
+        acc[1] += vol * H;
+        acc[2] += vol * C;
+        acc[3] += vol * (clamp01(C) * (1.0 - Fl));
         const double mx = (double)w.mx, my = (double)w.my;
         acc[4] = fmax(acc[4], sqrt(mx * mx + my * my) / (rho * (1.0 / 3.0)));
         if (!(isfinite(H) && isfinite(C) && isfinite((double)w.p) && isfinite(mx) && isfinite(my))) acc[5] = 1.0;

@@ -91,10 +91,27 @@ __device__ __forceinline__ void load_rows(Smem<R>& S, const R* in, int x0, int r
     }
 }
 
-// Step 2: mu_c (reading R5, 5-point Laplacian) for rows [r0, r0 + nrows),
-// columns 1 .. RW-2.  A wall ghost (layer 1 or 2) evaluates the Laplacian at
-// its mirror cell, which equals mirroring the interior value; deeper layers
-// are never read by a face of the strip and get 0.
+// mu_c = 2 beta C (C-1)(2C-1) - kappa lap C (reading R5) at ring offset s0
+// (column gx of the domain) with the y-neighbours at sN, sS.  The Laplacian
+// is the 5-point one, or in an axisymmetric domain the conservative
+// (1/r) d/dr (r dC/dr) + d2C/dz2 with faces at r = gx and gx + 1.
+template <class R>
+__device__ __forceinline__ R chem_potential(const Consts<R>& K, const R* C, int s0, int sN, int sS, int gx) {
+    const R c = C[s0];
+    R lap;
+    if (K.axi) {
+        const R rw = (R)gx, re = rw + R(1);
+        lap = wdiv(re * (C[s0 + 1] - c) - rw * (c - C[s0 - 1]), rw + R(0.5)) + (C[sN] + C[sS] - R(2) * c);
+    } else {
+        lap = C[s0 + 1] + C[s0 - 1] + C[sN] + C[sS] - R(4) * c;
+    }
+    return R(2) * K.beta * c * (c - R(1)) * (R(2) * c - R(1)) - K.kappa * lap;
+}
+
+// Step 2: mu_c for rows [r0, r0 + nrows), columns 1 .. RW-2.  A wall ghost
+// (layer 1 or 2) evaluates mu_c at its mirror cell, which equals mirroring
+// the interior value; deeper layers are never read by a face of the strip
+// and get 0.
 template <class R>
 __device__ __forceinline__ void muc_rows(Smem<R>& S, int x0, int r0, int nrows) {
     const Consts<R>& K = S.K;
@@ -107,9 +124,8 @@ __device__ __forceinline__ void muc_rows(Smem<R>& S, int x0, int r0, int nrows) 
             const int rr = idx / NC, cc = 1 + idx - rr * NC;
             const int gy = r0 + rr;
             const int s0 = slot(gy) * RW + cc;
-            const R c = C[s0];
-            const R lap = C[s0 + 1] + C[s0 - 1] + C[slot(gy + 1) * RW + cc] + C[slot(gy - 1) * RW + cc] - R(4) * c;
-            S.P[F_MUC][slot(gy)][cc] = R(2) * K.beta * c * (c - R(1)) * (R(2) * c - R(1)) - K.kappa * lap;
+            S.P[F_MUC][slot(gy)][cc] =
+                chem_potential(K, C, s0, slot(gy + 1) * RW + cc, slot(gy - 1) * RW + cc, x0 + cc - kHalo);
         }
         return;
     }
@@ -126,12 +142,9 @@ __device__ __forceinline__ void muc_rows(Smem<R>& S, int x0, int r0, int nrows) 
             else if (gy >= K.ny) { const int k = gy - K.ny + 1; my = gy - (2 * k - 1); deep |= k > 2; }
         }
         R mu = R(0);
-        if (!deep) {
-            const int s0 = slot(my) * RW + mc;
-            const R c = C[s0];
-            const R lap = C[s0 + 1] + C[s0 - 1] + C[slot(my + 1) * RW + mc] + C[slot(my - 1) * RW + mc] - R(4) * c;
-            mu = R(2) * K.beta * c * (c - R(1)) * (R(2) * c - R(1)) - K.kappa * lap;
-        }
+        if (!deep)
+            mu = chem_potential(K, C, slot(my) * RW + mc, slot(my + 1) * RW + mc, slot(my - 1) * RW + mc,
+                                x0 + mc - kHalo);
         S.P[F_MUC][slot(gy)][cc] = mu;
     }
 }
@@ -203,8 +216,15 @@ __device__ __forceinline__ R face_value(const R* f, const FaceIdx& x) {
 //   C_ref T part of sum e_n h = C_ref (T_L - T_R)/6
 // (dp = central t-difference), and the nonlinear parts (rho q, C e.u,
 // C_p T q, q) are summed point by point with one multiply per weight class.
+//
+// Axisymmetric domains (reading R24): the face pressure is advanced with the
+// axisymmetric mass source -rho cs^2 u_r / r as well, streamed with weight
+// w_a over dt_s.  Of the fluxes only the normal momentum flux changes, by
+// cs^2 dt_s (-rho_f cs^2 u_r / r) = -rho_f u_r / (18 r) with the face values;
+// inv_r = 1 / r of the face (0 on the axis, where the face area is zero).
 template <class R>
-__device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const R* P, const FaceIdx& x, int fUn, int fUt) {
+__device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const R* P, const FaceIdx& x, int fUn, int fUt,
+                                                 bool normal_is_r, R inv_r) {
     R un[9], ut[9], rr[9], CC[9];
     all_points(rec(P + fUn * FS, x), un);
     all_points(rec(P + fUt * FS, x), ut);
@@ -299,13 +319,15 @@ __device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const R* P,
     F.Fmt = (R(1) - tf) * cs2 * rho_f * unf * utf + tf * (Snt_p + rho_f * Snt_q);
     F.Fc = (R(1) - tg) * Cf * unf + tg * Sg;     // Eq. 44, 46
     F.un = unf;
+    if (K.axi) F.Fmn += R(-1.0 / 18.0) * rho_f * (normal_is_r ? un[0] : ut[0]) * inv_r;
     return F;
 }
 
 // Step 3, x-faces of ring row r: lane l computes the face between columns
-// l+2 and l+3 (cells x0+l-1 and x0+l).
+// l+2 and l+3 (cells x0+l-1 and x0+l), at x = x0 + l.  In an axisymmetric
+// domain the stored fluxes are multiplied by the face area r_f = x0 + l.
 template <class R>
-__device__ __forceinline__ void x_face(Smem<R>& S, int r, int row_in_chunk, int lane) {
+__device__ __forceinline__ void x_face(Smem<R>& S, int x0, int r, int row_in_chunk, int lane) {
     FaceIdx x;
     const int cL = lane + 2;
     x.L = slot(r) * RW + cL;
@@ -316,7 +338,12 @@ __device__ __forceinline__ void x_face(Smem<R>& S, int r, int row_in_chunk, int 
     x.Lm = slot(r - 1) * RW + cL;
     x.Rp = x.Lp + 1;
     x.Rm = x.Lm + 1;
-    const FaceFlux<R> F = face_flux(S.K, &S.P[0][0][0], x, F_U, F_V);
+    const int gf = x0 + lane;
+    const R rf = S.K.axi ? (R)gf : R(1);
+    FaceFlux<R> F = face_flux(S.K, &S.P[0][0][0], x, F_U, F_V, true, gf > 0 ? wdiv(R(1), rf) : R(0));
+    if (S.K.axi) {
+        F.Fh *= rf; F.Fp *= rf; F.Fmn *= rf; F.Fmt *= rf; F.Fc *= rf; F.un *= rf;
+    }
     S.XF[0][row_in_chunk][lane] = F.Fh;
     S.XF[1][row_in_chunk][lane] = F.Fp;
     S.XF[2][row_in_chunk][lane] = F.Fmn;   // x-momentum
@@ -325,9 +352,10 @@ __device__ __forceinline__ void x_face(Smem<R>& S, int r, int row_in_chunk, int 
     S.XF[5][row_in_chunk][lane] = F.un;
 }
 
-// Step 3, y-faces of face row r (between rows r-1 and r), lane l < 31 at column l+3.
+// Step 3, y-faces of face row r (between rows r-1 and r), lane l < 31 at
+// column l+3 (cell x0 + l, radius x0 + l + 1/2 in an axisymmetric domain).
 template <class R>
-__device__ __forceinline__ void y_face(Smem<R>& S, int r, int lane) {
+__device__ __forceinline__ void y_face(Smem<R>& S, int x0, int r, int lane) {
     FaceIdx x;
     const int c = lane + kHalo;
     x.L = slot(r - 1) * RW + c;
@@ -338,7 +366,8 @@ __device__ __forceinline__ void y_face(Smem<R>& S, int r, int lane) {
     x.Lm = x.L - 1;
     x.Rp = x.R + 1;
     x.Rm = x.R - 1;
-    const FaceFlux<R> F = face_flux(S.K, &S.P[0][0][0], x, F_V, F_U);
+    const R inv_r = S.K.axi ? wdiv(R(1), (R)(x0 + lane) + R(0.5)) : R(0);
+    const FaceFlux<R> F = face_flux(S.K, &S.P[0][0][0], x, F_V, F_U, false, inv_r);
     const int s = slot(r);
     S.YF[0][s][lane] = F.Fh;
     S.YF[1][s][lane] = F.Fp;
@@ -358,11 +387,17 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
     const int q = slot(r) * RW + lane + kHalo;
     const int qn = slot(r + 1) * RW + lane + kHalo, qs = slot(r - 1) * RW + lane + kHalo;
     const int sr = slot(r), sn = slot(r + 1);
+    // Eq. 52; axisymmetric: the x-face fluxes carry their areas r_f, divided
+    // here by the cell volume r_i = gx + 1/2 (per radian)
+    const R irc = K.axi ? wdiv(R(1), (R)gx + R(0.5)) : R(1);
     R Rk[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k)
-        Rk[k] = -((S.XF[k][row_in_chunk][lane + 1] - S.XF[k][row_in_chunk][lane]) + (S.YF[k][sn][lane] - S.YF[k][sr][lane]));
-    const R divu = (S.XF[5][row_in_chunk][lane + 1] - S.XF[5][row_in_chunk][lane]) + (S.YF[5][sn][lane] - S.YF[5][sr][lane]);
+        Rk[k] = -((S.XF[k][row_in_chunk][lane + 1] - S.XF[k][row_in_chunk][lane]) * irc +
+                  (S.YF[k][sn][lane] - S.YF[k][sr][lane]));
+    const R divu =
+        (S.XF[5][row_in_chunk][lane + 1] - S.XF[5][row_in_chunk][lane]) * irc + (S.YF[5][sn][lane] - S.YF[5][sr][lane]);
+    const R divF1 = -Rk[1];   // div(rho cs^2 u), the pressure-flux divergence
 
     const R* P = &S.P[0][0][0];
     const R T = P[F_T * FS + q], Fl = P[F_FL * FS + q], Cp = P[F_CP * FS + q];
@@ -388,6 +423,8 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
     Rk[2] += cs2 * (-Fl * C * dmx + rho * K.gx - rho * u * D);         // row 3 (R13)
     Rk[3] += cs2 * (-Fl * C * dmy + rho * K.gy - rho * v * D);         // row 4
     Rk[4] += C * K.kv * D;                                             // row 5 (R12)
+    if (K.axi)   // hoop stress Pi_thetatheta / r with the pressure advanced over dt_s (reading R24)
+        Rk[2] += cs2 * (P[F_P * FS + q] - R(0.5) * divF1 - R(2) * P[F_MU * FS + q] * u * irc) * irc;
 
     const R* in = reinterpret_cast<const R*>(K.st[stage]);
     const SV<R> ws = load_state(in, K.plane, c);
@@ -469,7 +506,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) stage_kernel(Stage
         __syncthreads();
         muc_rows(S, x0, y0 - 2, 4);
         __syncthreads();
-        if (warp == 0 && lane < kStripX) y_face(S, y0, lane);
+        if (warp == 0 && lane < kStripX) y_face(S, x0, y0, lane);
         // (the first chunk writes other ring rows: no barrier needed here)
 
         for (int j0 = y0; j0 < y1; j0 += kChunk) {
@@ -480,8 +517,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) stage_kernel(Stage
             // one face at a time per thread (x then y) keeps register use low
 #pragma unroll 1
             for (int k = 0; k < 2; ++k) {
-                if (k == 0) x_face(S, j0 + warp, warp, lane);
-                else if (lane < kStripX) y_face(S, j0 + 1 + warp, lane);
+                if (k == 0) x_face(S, x0, j0 + warp, warp, lane);
+                else if (lane < kStripX) y_face(S, x0, j0 + 1 + warp, lane);
             }
             __syncthreads();
             const int r = j0 + warp;

@@ -52,7 +52,7 @@ class BC(ct.Structure):
 
 
 class Numerics(ct.Structure):
-    _fields_ = [("dt", ct.c_double)]
+    _fields_ = [("dt", ct.c_double), ("axisymmetric", ct.c_int)]
 
 
 _DP = ct.POINTER(ct.c_double)
@@ -159,7 +159,7 @@ def domain_struct(case, keep: list) -> Domain:
     init = Init(*[_ptr(arrs[k]) for k in ("T", "Fl", "C", "u", "v", "p")])
     if abs(case.dt_stream - 0.5) > 0:
         raise ValueError("libeulbfs uses the streaming step dt_s = 0.5 (lattice units)")
-    return Domain(Grid(case.nx, case.ny), _props(case.props), _bc(case.bc), Numerics(case.dt), init)
+    return Domain(Grid(case.nx, case.ny), _props(case.props), _bc(case.bc), Numerics(case.dt, int(getattr(case, "axisymmetric", 0))), init)
 
 
 class Solver:

@@ -211,9 +211,11 @@ def film(n: int = 512, seed: int = 3, dt: float = 0.5, height: float = 0.3,
 # ---------------------------------------------------------------------------
 def droplet(side: int, theta_deg: float = 90.0, St: float = 0.2, rho_sl: float = 0.917,
             Tw: float = -0.5, dt: float = 0.5, name: str | None = None,
-            impact_speed: float = 0.0, We: float | None = None, Re: float | None = None) -> Case:
-    """Half droplet of radius 0.25*side on the plate y = 0, symmetry plane at
-    x = 0 (planar stand-in for the axisymmetric (r, z) domain, reading R18).
+            impact_speed: float = 0.0, We: float | None = None, Re: float | None = None,
+            axisymmetric: bool = False) -> Case:
+    """Half droplet of radius 0.25*side on the plate y = 0 with its axis at
+    x = 0: a planar 2-D drop with a symmetry plane there, or with
+    axisymmetric=True the drop of revolution in (r, z) (reading R18).
     Plate at Tw < T_m = 0, liquid and gas initially at T_m; rho_l/rho_g = 1000.
     With impact_speed U > 0 the drop is released at rest 0.1*side above the
     plate under gravity g = U^2 / (2 gap), reaching U at contact (an impulsive
@@ -255,23 +257,25 @@ def droplet(side: int, theta_deg: float = 90.0, St: float = 0.2, rho_sl: float =
     dist = np.sqrt(x[None, :] ** 2 + (y[:, None] - y0) ** 2)
     C = 0.5 * (1.0 + np.tanh(2.0 * (R - dist) / props.xi))   # Eq. 62 read as a circle (R20)
     init = _fields(side, side, T=Tm, Fl=1.0, C=C)
-    return Case(name or f"droplet_{side}", side, side, props, bc, dt, init)
+    tag = "_rz" if axisymmetric else ""
+    return Case(name or f"droplet_{side}{tag}", side, side, props, bc, dt, init, axisymmetric=int(axisymmetric))
 
 
 BATCH_SIDES = (128, 192, 256, 384, 512)
 
 
-def static_droplet_batch(n: int = 64, seed: int = 4, sides=BATCH_SIDES) -> List[Case]:
+def static_droplet_batch(n: int = 64, seed: int = 4, sides=BATCH_SIDES, axisymmetric: bool = False) -> List[Case]:
     """n droplet domains, side uniform over `sides`, seeded contact angle in
     [60, 150] deg, St in [0.05, 0.5], rho_s/rho_l in [0.85, 0.95] and plate
-    temperature in [-1, -0.2] (melting point 0)."""
+    temperature in [-1, -0.2] (melting point 0); planar or axisymmetric."""
     rng = np.random.default_rng(seed)
     out = []
     for k in range(n):
         side = int(rng.choice(sides))
         out.append(droplet(side, theta_deg=float(rng.uniform(60, 150)),
                            St=float(rng.uniform(0.05, 0.5)), rho_sl=float(rng.uniform(0.85, 0.95)),
-                           Tw=float(rng.uniform(-1.0, -0.2)), name=f"drop{k}_{side}"))
+                           Tw=float(rng.uniform(-1.0, -0.2)), name=f"drop{k}_{side}",
+                           axisymmetric=axisymmetric))
     return out
 
 
@@ -287,7 +291,8 @@ class Request:
 
 
 def impact_requests(n: int = 500, rate_hz: float = 20.0, seed: int = 5, lo: int = 256,
-                    hi: int = 1024, U: float = 0.05, end_time_UD: float = 0.015) -> List[Request]:
+                    hi: int = 1024, U: float = 0.05, end_time_UD: float = 0.015,
+                    axisymmetric: bool = False) -> List[Request]:
     """Poisson arrivals; side uniform in [lo, hi] rounded to 32; seeded We in
     [10, 200], Re in [100, 2000], St in [0.05, 0.5]; impact speed U (lattice)
     with D = side/2, rho_l/rho_g = 1000, rho_s/rho_l = 0.917.  Each request
@@ -303,7 +308,7 @@ def impact_requests(n: int = 500, rate_hz: float = 20.0, seed: int = 5, lo: int 
         Re = float(rng.uniform(100, 2000))
         St = float(rng.uniform(0.05, 0.5))
         case = droplet(side, theta_deg=90.0, St=St, rho_sl=0.917, Tw=-1.0, impact_speed=U,
-                       We=We, Re=Re, name=f"impact{k}_{side}")
+                       We=We, Re=Re, name=f"impact{k}_{side}", axisymmetric=axisymmetric)
         D = 0.5 * side
         steps = max(1, int(round(end_time_UD * D / U / case.dt)))
         reqs.append(Request(k, t, case, steps))

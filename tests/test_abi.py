@@ -70,4 +70,10 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     case.bc.yhi = wl.Side(wl.ADIABATIC, wl.NOSLIP, wl.NOFLUX)
     d = eulbfs.domain_struct(case, keep)
     assert lib.eulbfs_batch_create(1, ct.byref(d), eulbfs.FP64, None, ct.byref(h)) == eulbfs.EINVAL
+    # an axisymmetric domain needs its axis (xlo) adiabatic, symmetric and no-flux
+    case = wl.conductive(32, 2)
+    case.axisymmetric = 1
+    d = eulbfs.domain_struct(case, keep)
+    assert lib.eulbfs_batch_create(1, ct.byref(d), eulbfs.FP64, None, ct.byref(h)) == eulbfs.EINVAL
+    assert b"axis" in lib.eulbfs_last_error()
     assert lib.eulbfs_step(None, 1) == eulbfs.EINVAL

@@ -26,13 +26,13 @@ def _built():
     oracle.build()
 
 
-def assert_fields_close(g, r, rtol, keys=FIELDS, what=""):
-    """Max-norm error of each field relative to the field's magnitude; the two
-    velocity components share the speed scale (one is pure round-off noise in
-    the quasi-1D problems)."""
-    speed = max(float(np.max(np.abs(r["u"]))), float(np.max(np.abs(r["v"]))), 1e-12)
+def assert_fields_close(g, r, rtol, keys=FIELDS, what="", floor=1e-12):
+    """Max-norm error of each field relative to the field's magnitude (at
+    least `floor`); the two velocity components share the speed scale (one is
+    pure round-off noise in the quasi-1D problems)."""
+    speed = max(float(np.max(np.abs(r["u"]))), float(np.max(np.abs(r["v"]))), floor)
     for k in keys:
-        scale = speed if k in ("u", "v") else max(float(np.max(np.abs(r[k]))), 1e-12)
+        scale = speed if k in ("u", "v") else max(float(np.max(np.abs(r[k]))), floor)
         err = float(np.max(np.abs(g[k] - r[k])))
         assert err <= rtol * scale, f"{what} field {k}: max|gpu - oracle| = {err:.3e} > {rtol:g} * {scale:.3e}"
 

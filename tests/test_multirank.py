@@ -64,7 +64,7 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
 
     class Args:
-        domains, seed, warmup, steps, gpus, tile, graph = 2, 4, 0, 1, 2, 64, 0
+        domains, seed, warmup, steps, gpus, tile, graph, geometry = 2, 4, 0, 1, 2, 64, 0, "rz"
 
     assert bench.run_reference(Args) == 0
     assert capsys.readouterr().out == ""
