@@ -54,7 +54,7 @@ class Props(ct.Structure):
 
 class Side(ct.Structure):
     _fields_ = [("thermal", ct.c_int), ("flow", ct.c_int), ("phase", ct.c_int), ("Tw", ct.c_double),
-                ("theta_deg", ct.c_double)]
+                ("theta_deg", ct.c_double), ("theta_adv_deg", ct.c_double), ("theta_rec_deg", ct.c_double)]
 
 
 class BC(ct.Structure):
@@ -125,7 +125,8 @@ def props_struct(p) -> Props:
 
 
 def bc_struct(b) -> BC:
-    sd = lambda q: Side(q.thermal, q.flow, q.phase, q.Tw, q.theta_deg)  # noqa: E731
+    sd = lambda q: Side(q.thermal, q.flow, q.phase, q.Tw, q.theta_deg,  # noqa: E731
+                        getattr(q, "theta_adv_deg", q.theta_deg), getattr(q, "theta_rec_deg", q.theta_deg))
     return BC(sd(b.xlo), sd(b.xhi), sd(b.ylo), sd(b.yhi))
 
 

@@ -190,8 +190,46 @@ static void derive_interior(or_solver* s, double* const W[5]) {
 /* Ghost value k layers outside a wall side from the value vm in its mirror
  * cell.  The boundary conditions act directly on macroscopic variables.
  * normal_f is the wall-normal velocity component. */
+/* Reading R25, contact-angle hysteresis (Sec. 3.5 gives theta_adv and theta_r
+ * but no model; this is a literature-style choice).  The apparent angle at
+ * the wall position t (the row of an x side, the column of a y side, clamped
+ * to the domain or wrapped on a periodic axis) is read from the phase field
+ * of the two wall layers: cos(theta_app) = dC/dn_out / |grad C| with
+ * dC/dn_out = C_0 - C_1 and the tangential central difference along layer 0
+ * (one-sided at a walled end).  The wetting rule of R11 then takes
+ * cos(theta) = cos(theta_app) clamped to [cos(theta_adv), cos(theta_rec)]:
+ * inside that window the contact line keeps its current angle (pinned),
+ * outside it the nearer limit applies.  Where |grad C| vanishes (no
+ * interface at the wall) the equilibrium angle is used. */
+static double wall_cos_theta(const or_solver* s, const or_side* sd, int side, int t) {
+    const double ceq = cos(sd->theta_deg * (M_PI / 180.0));
+    if (sd->phase != OR_BC_WETTING_HYST) return ceq;
+    const int xs = side < 2;                       /* an x side: t runs along y */
+    const int n = xs ? s->ny : s->nx, m = xs ? s->nx : s->ny;
+    const int per = xs ? (s->B.ylo.thermal == OR_BC_PERIODIC) : (s->B.xlo.thermal == OR_BC_PERIODIC);
+    int tc = t, tp = t + 1, tm = t - 1;
+    if (per) {
+        tc = wrapi(t, n); tp = wrapi(t + 1, n); tm = wrapi(t - 1, n);
+    } else {
+        tc = t < 0 ? 0 : (t > n - 1 ? n - 1 : t);
+        tp = tc + 1 > n - 1 ? n - 1 : tc + 1;
+        tm = tc - 1 < 0 ? 0 : tc - 1;
+    }
+    const int l0 = (side == 0 || side == 2) ? 0 : m - 1;     /* wall layer and the one inside */
+    const int l1 = (side == 0 || side == 2) ? 1 : m - 2;
+    const double* C = s->prim[P_C];
+#define CAT(layer, tt) (xs ? C[PI(s, (layer), (tt))] : C[PI(s, (tt), (layer))])
+    const double dn = CAT(l0, tc) - CAT(l1, tc);
+    const double dt = per ? 0.5 * (CAT(l0, tp) - CAT(l0, tm)) : (CAT(l0, tp) - CAT(l0, tm)) / (double)(tp - tm);
+#undef CAT
+    const double g = sqrt(dn * dn + dt * dt);
+    if (!(g > 1e-12)) return ceq;
+    const double c = dn / g, lo = cos(sd->theta_adv_deg * (M_PI / 180.0)), hi = cos(sd->theta_rec_deg * (M_PI / 180.0));
+    return c < lo ? lo : (c > hi ? hi : c);
+}
+
 static double ghost_value(const or_solver* s, const or_side* sd, int f, int k, int normal_f,
-                          double vm) {
+                          double vm, double cth) {
     switch (f) {
         case P_T: return sd->thermal == OR_BC_DIRICHLET_T ? 2.0 * sd->Tw - vm : vm;
         case P_P: return sd->flow == OR_BC_OUTLET ? -vm : vm;
@@ -201,10 +239,10 @@ static double ghost_value(const or_solver* s, const or_side* sd, int f, int k, i
             if (sd->flow == OR_BC_SYMMETRY) return f == normal_f ? -vm : vm;
             return vm;
         case P_C:
-            if (sd->phase == OR_BC_WETTING) {
-                /* R11: dC/dn_out = (4 cos(theta)/xi) C (1 - C), ghost k at distance (2k-1) */
-                const double th = sd->theta_deg * (M_PI / 180.0);
-                return vm + (2.0 * k - 1.0) * (4.0 * cos(th) / s->P.xi) * vm * (1.0 - vm);
+            if (sd->phase == OR_BC_WETTING || sd->phase == OR_BC_WETTING_HYST) {
+                /* R11: dC/dn_out = (4 cos(theta)/xi) C (1 - C), ghost k at distance (2k-1);
+                 * cth = cos(theta) of this wall position (R25 for hysteresis) */
+                return vm + (2.0 * k - 1.0) * (4.0 * cth / s->P.xi) * vm * (1.0 - vm);
             }
             return vm;
         default: return vm;   /* H, F_l, properties, mu_c: mirror copy */
@@ -222,11 +260,13 @@ static void fill_ghosts(or_solver* s, const int* fields, int nf) {
             const int gl = -k, gh = nx - 1 + k;
             const int ml = perx ? wrapi(gl, nx) : k - 1;
             const int mh = perx ? wrapi(gh, nx) : nx - k;
+            const double cl = perx ? 0.0 : wall_cos_theta(s, &s->B.xlo, 0, j);
+            const double ch = perx ? 0.0 : wall_cos_theta(s, &s->B.xhi, 1, j);
             for (int n = 0; n < nf; ++n) {
                 const int f = fields[n];
                 const double vl = s->prim[f][PI(s, ml, j)], vh = s->prim[f][PI(s, mh, j)];
-                s->prim[f][PI(s, gl, j)] = perx ? vl : ghost_value(s, &s->B.xlo, f, k, P_U, vl);
-                s->prim[f][PI(s, gh, j)] = perx ? vh : ghost_value(s, &s->B.xhi, f, k, P_U, vh);
+                s->prim[f][PI(s, gl, j)] = perx ? vl : ghost_value(s, &s->B.xlo, f, k, P_U, vl, cl);
+                s->prim[f][PI(s, gh, j)] = perx ? vh : ghost_value(s, &s->B.xhi, f, k, P_U, vh, ch);
             }
         }
     for (int i = -NG; i < nx + NG; ++i)
@@ -234,11 +274,13 @@ static void fill_ghosts(or_solver* s, const int* fields, int nf) {
             const int gl = -k, gh = ny - 1 + k;
             const int ml = pery ? wrapi(gl, ny) : k - 1;
             const int mh = pery ? wrapi(gh, ny) : ny - k;
+            const double cl = pery ? 0.0 : wall_cos_theta(s, &s->B.ylo, 2, i);
+            const double ch = pery ? 0.0 : wall_cos_theta(s, &s->B.yhi, 3, i);
             for (int n = 0; n < nf; ++n) {
                 const int f = fields[n];
                 const double vl = s->prim[f][PI(s, i, ml)], vh = s->prim[f][PI(s, i, mh)];
-                s->prim[f][PI(s, i, gl)] = pery ? vl : ghost_value(s, &s->B.ylo, f, k, P_V, vl);
-                s->prim[f][PI(s, i, gh)] = pery ? vh : ghost_value(s, &s->B.yhi, f, k, P_V, vh);
+                s->prim[f][PI(s, i, gl)] = pery ? vl : ghost_value(s, &s->B.ylo, f, k, P_V, vl, cl);
+                s->prim[f][PI(s, i, gh)] = pery ? vh : ghost_value(s, &s->B.yhi, f, k, P_V, vh, ch);
             }
         }
 }
@@ -481,7 +523,10 @@ static int check_side(const or_side* sd, int periodic) {
     if (sd->thermal != OR_BC_DIRICHLET_T && sd->thermal != OR_BC_ADIABATIC) return 0;
     if (sd->flow != OR_BC_NOSLIP && sd->flow != OR_BC_SYMMETRY && sd->flow != OR_BC_OUTLET)
         return 0;
-    if (sd->phase != OR_BC_NOFLUX && sd->phase != OR_BC_WETTING) return 0;
+    if (sd->phase != OR_BC_NOFLUX && sd->phase != OR_BC_WETTING && sd->phase != OR_BC_WETTING_HYST) return 0;
+    if (sd->phase == OR_BC_WETTING_HYST &&
+        !(sd->theta_rec_deg >= 0.0 && sd->theta_rec_deg <= sd->theta_adv_deg && sd->theta_adv_deg <= 180.0))
+        return 0;
     return 1;
 }
 

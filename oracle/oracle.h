@@ -52,10 +52,13 @@ enum {
     OR_BC_SYMMETRY = 4,    /* flow: normal u = 0, zero gradient of tangential u */
     OR_BC_OUTLET = 5,      /* flow: p = 0 on the face, zero gradient of u */
     OR_BC_NOFLUX = 6,      /* phase: zero normal gradient of C and mu_c */
-    OR_BC_WETTING = 7      /* phase: contact angle theta (reading R11) */
+    OR_BC_WETTING = 7,     /* phase: contact angle theta (reading R11) */
+    OR_BC_WETTING_HYST = 8 /* phase: contact angle within [theta_rec, theta_adv] (reading R25) */
 };
 
-typedef struct { int thermal, flow, phase; double Tw, theta_deg; } or_side;
+/* theta_deg: (equilibrium) contact angle; theta_adv_deg >= theta_rec_deg bound
+ * the apparent angle for OR_BC_WETTING_HYST. */
+typedef struct { int thermal, flow, phase; double Tw, theta_deg, theta_adv_deg, theta_rec_deg; } or_side;
 typedef struct { or_side xlo, xhi, ylo, yhi; } or_bc;
 
 typedef struct {

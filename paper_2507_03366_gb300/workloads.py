@@ -20,7 +20,7 @@ from typing import Dict, List
 import numpy as np
 
 # Boundary-condition kinds.  The numeric values are the ones of the C ABI.
-PERIODIC, DIRICHLET_T, ADIABATIC, NOSLIP, SYMMETRY, OUTLET, NOFLUX, WETTING = range(8)
+PERIODIC, DIRICHLET_T, ADIABATIC, NOSLIP, SYMMETRY, OUTLET, NOFLUX, WETTING, WETTING_HYST = range(9)
 
 
 @dataclass
@@ -55,6 +55,14 @@ class Side:
     phase: int
     Tw: float = 0.0
     theta_deg: float = 90.0
+    theta_adv_deg: float | None = None     # WETTING_HYST: advancing and receding limits
+    theta_rec_deg: float | None = None     # (None: the equilibrium angle)
+
+    def __post_init__(self):
+        if self.theta_adv_deg is None:
+            self.theta_adv_deg = self.theta_deg
+        if self.theta_rec_deg is None:
+            self.theta_rec_deg = self.theta_deg
 
 
 @dataclass

@@ -15,6 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "eulbfs_oracle.c")
 PINS = "tests/test_oracle_pins.py::"
 AXI = "tests/test_oracle_axisymmetric.py::"
+HYS = "tests/test_oracle_hysteresis.py::"
 
 # (name, original text, planted text, pin that must fail)
 MUTATIONS = [
@@ -81,6 +82,13 @@ MUTATIONS = [
      AXI + "test_laplacian_of_r_squared"),
     ("axi_volume_weight", "const double w = s->N.axisymmetric ? (c % s->nx) + 0.5 : 1.0;",
      "const double w = s->N.axisymmetric ? (c % s->nx) + 1.0 : 1.0;", AXI + "test_sphere_volume_and_gibbs_thomson"),
+    # contact-angle hysteresis (reading R25)
+    ("hysteresis_normal_sign", "const double dn = CAT(l0, tc) - CAT(l1, tc);",
+     "const double dn = CAT(l1, tc) - CAT(l0, tc);", HYS + "test_contact_line_pinned_inside_window"),
+    ("hysteresis_tangential_dropped", "const double g = sqrt(dn * dn + dt * dt);", "const double g = fabs(dn) + 0.0 * dt;",
+     HYS + "test_contact_line_pinned_inside_window"),
+    ("hysteresis_limits_swapped", "return c < lo ? lo : (c > hi ? hi : c);", "return c < hi ? hi : (c > lo ? lo : c);",
+     HYS + "test_limits_act_as_static_angles_outside_window"),
 ]
 
 
