@@ -199,8 +199,10 @@ static void derive_interior(or_solver* s, double* const W[5]) {
  * (one-sided at a walled end).  The wetting rule of R11 then takes
  * cos(theta) = cos(theta_app) clamped to [cos(theta_adv), cos(theta_rec)]:
  * inside that window the contact line keeps its current angle (pinned),
- * outside it the nearer limit applies.  Where |grad C| vanishes (no
- * interface at the wall) the equilibrium angle is used. */
+ * outside it the nearer limit applies.  Where the wall cell carries no
+ * interface, C_0 (1 - C_0) < 1e-3, the equilibrium angle is used: there the
+ * direction of grad C is set by round-off and the R11 correction, which
+ * scales with C (1 - C), is negligible anyway. */
 static double wall_cos_theta(const or_solver* s, const or_side* sd, int side, int t) {
     const double ceq = cos(sd->theta_deg * (M_PI / 180.0));
     if (sd->phase != OR_BC_WETTING_HYST) return ceq;
@@ -221,9 +223,11 @@ static double wall_cos_theta(const or_solver* s, const or_side* sd, int side, in
 #define CAT(layer, tt) (xs ? C[PI(s, (layer), (tt))] : C[PI(s, (tt), (layer))])
     const double dn = CAT(l0, tc) - CAT(l1, tc);
     const double dt = per ? 0.5 * (CAT(l0, tp) - CAT(l0, tm)) : (CAT(l0, tp) - CAT(l0, tm)) / (double)(tp - tm);
+    const double c0 = CAT(l0, tc);
+    if (!(c0 * (1.0 - c0) >= 1e-3)) return ceq;
 #undef CAT
     const double g = sqrt(dn * dn + dt * dt);
-    if (!(g > 1e-12)) return ceq;
+    if (!(g > 0.0)) return ceq;
     const double c = dn / g, lo = cos(sd->theta_adv_deg * (M_PI / 180.0)), hi = cos(sd->theta_rec_deg * (M_PI / 180.0));
     return c < lo ? lo : (c > hi ? hi : c);
 }
