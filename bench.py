@@ -32,15 +32,19 @@ import numpy as np  # noqa: E402
 
 BYTES_PER_CELL_STEP = {1: 244, 0: 352}    # algorithmic HBM bytes per cell per time step (FP32C, FP64)
 STAGES = 3
-# FP32 operations per cell per stage of the FP32C stage kernel (FFMA counted
-# as 2), from the ncu instruction counters of one capture; the formulation's
-# arithmetic, so it changes only when the face/cell algebra changes.
-FP32_FLOPS_PER_CELL_STAGE = 1100
+# Per cell and stage of the FP32C stage kernel, from the ncu counters of one
+# capture of each geometry (24 domains, 2.32 M cells, stages 0-2): FP32
+# operations (FFMA counted as 2) and warp instructions issued.  They are the
+# formulation's arithmetic and the kernel's instruction stream, so they change
+# only with the face/cell algebra or the code.
+FP32_FLOPS_PER_CELL_STAGE = {"rz": 1144, "xy": 1100}
+WARP_INST_PER_CELL_STAGE = {"rz": 52.8, "xy": 50.2}
 # DRAM bytes per cell per launch of the stage kernel (ncu, average of the 3
-# stages, 2.32 M-cell capture scaled by cells).
-DRAM_BYTES_PER_CELL_LAUNCH = 64.4
-# FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x SM clock.
-SMS, FP32_LANES_PER_SM = 152, 128
+# stages of the same capture, scaled by cells).
+DRAM_BYTES_PER_CELL_LAUNCH = 64.5
+# Peaks from unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x SM clock;
+# 4 warp instructions issued per SM per clock (one per scheduler).
+SMS, FP32_LANES_PER_SM, ISSUE_PER_SM_CLK = 152, 128, 4
 
 
 def parse():
@@ -266,7 +270,7 @@ def main():
     launches = STAGES * args.steps
 
     # ---- roofline of the stage kernel (the only kernel in the region) --------
-    # Arithmetic intensity 1100 flop / 81.3 B = 13.5 flop/B is above the
+    # Arithmetic intensity ~1100 flop / 81.3 B = 13.5 flop/B is above the
     # machine balance (80.5 TFLOP/s / 6.68 TB/s = 12 flop/B): FP32 ALU roof.
     peaks = measured_peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
@@ -275,15 +279,20 @@ def main():
     per_launch_ms = ms / launches
     alg_bytes = BYTES_PER_CELL_STEP[1] / STAGES * cells
     achieved_gbs = alg_bytes / (per_launch_ms * 1e-3) / 1e9
-    flops = FP32_FLOPS_PER_CELL_STAGE * cells
+    flops = FP32_FLOPS_PER_CELL_STAGE[args.geometry] * cells
     achieved_tf = flops / (per_launch_ms * 1e-3) / 1e12
+    issue_peak = SMS * ISSUE_PER_SM_CLK * clk_mhz * 1e6
+    issue = WARP_INST_PER_CELL_STAGE[args.geometry] * cells / (per_launch_ms * 1e-3)
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved_tf / fp32_peak, "traffic": DRAM_BYTES_PER_CELL_LAUNCH * cells,
                 "peak_source": "unit counts x max SM clock (152 x 128 x 2 x %.0f MHz)" % clk_mhz,
                 "kernel": "eulbfs::stage_kernel<float>", "flops_per_launch": flops, "avg_launch_ms": per_launch_ms,
                 "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
                         "peak_source": "measured" if peaks else "fallback",
-                        "algorithmic_bytes_per_launch": alg_bytes}}
+                        "algorithmic_bytes_per_launch": alg_bytes},
+                "issue": {"achieved": issue, "peak": issue_peak, "unit": "warp-inst/s", "frac": issue / issue_peak,
+                          "peak_source": "152 SMs x 4 schedulers x %.0f MHz" % clk_mhz,
+                          "warp_inst_per_cell_stage": WARP_INST_PER_CELL_STAGE[args.geometry]}}
 
     # ---- FP64 plain GPU step on the same workload ------------------------------
     fp64 = None

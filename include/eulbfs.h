@@ -57,7 +57,15 @@ typedef enum {
     EULBFS_BC_SYMMETRY = 4,    /* flow: zero normal velocity, free slip */
     EULBFS_BC_OUTLET = 5,      /* flow: p = 0 on the face, zero gradient of u */
     EULBFS_BC_NOFLUX = 6,      /* phase field: zero normal gradient of C and mu_c */
-    EULBFS_BC_WETTING = 7      /* phase field: contact angle theta_deg */
+    EULBFS_BC_WETTING = 7,     /* phase field: contact angle theta_deg */
+    /* phase field: contact-angle hysteresis.  The apparent angle at each wall
+     * position, read from the two wall layers (cos = dC/dn_out / |grad C|),
+     * is clamped to [theta_rec_deg, theta_adv_deg] and used as the contact
+     * angle: inside that window the contact line is pinned, outside it the
+     * nearer limit applies (Sec. 3.5 quotes theta_adv and theta_r; the paper
+     * gives no model, this is one).  theta_deg is used where the wall layers
+     * carry no interface. */
+    EULBFS_BC_WETTING_HYST = 8
 } eulbfs_bc_kind;
 
 typedef struct { int nx, ny; } eulbfs_grid;   /* cells; nx, ny >= 2 on walled axes */
@@ -77,7 +85,12 @@ typedef struct {
     int zero_solid_velocity; /* 1: momentum of the solid part projected to zero */
 } eulbfs_props;
 
-typedef struct { int thermal, flow, phase; double Tw, theta_deg; } eulbfs_side;
+/* Tw: wall temperature (DIRICHLET_T).  theta_deg: contact angle (WETTING),
+ * or the angle where no interface touches the wall (WETTING_HYST).
+ * theta_adv_deg, theta_rec_deg: the hysteresis window of WETTING_HYST,
+ * 0 <= theta_rec_deg <= theta_adv_deg <= 180 (EINVAL otherwise); ignored by
+ * the other kinds. */
+typedef struct { int thermal, flow, phase; double Tw, theta_deg, theta_adv_deg, theta_rec_deg; } eulbfs_side;
 typedef struct { eulbfs_side xlo, xhi, ylo, yhi; } eulbfs_bc;
 
 typedef struct {

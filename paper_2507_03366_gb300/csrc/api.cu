@@ -68,7 +68,9 @@ bool valid_kind_side(const eulbfs_side& s, bool periodic) {
         return s.thermal == EULBFS_BC_PERIODIC && s.flow == EULBFS_BC_PERIODIC && s.phase == EULBFS_BC_PERIODIC;
     return (s.thermal == EULBFS_BC_DIRICHLET_T || s.thermal == EULBFS_BC_ADIABATIC) &&
            (s.flow == EULBFS_BC_NOSLIP || s.flow == EULBFS_BC_SYMMETRY || s.flow == EULBFS_BC_OUTLET) &&
-           (s.phase == EULBFS_BC_NOFLUX || s.phase == EULBFS_BC_WETTING);
+           (s.phase == EULBFS_BC_NOFLUX || s.phase == EULBFS_BC_WETTING ||
+            (s.phase == EULBFS_BC_WETTING_HYST && s.theta_rec_deg >= 0.0 && s.theta_rec_deg <= s.theta_adv_deg &&
+             s.theta_adv_deg <= 180.0));
 }
 
 int validate(const eulbfs_grid& g, const eulbfs_props& P, const eulbfs_bc& B, const eulbfs_numerics& N) {
@@ -108,6 +110,8 @@ DomainDesc make_desc(const eulbfs_grid& g, const eulbfs_props& P, const eulbfs_b
         d.bc_c[k] = sides[k]->phase;
         d.Tw[k] = sides[k]->Tw;
         d.wet[k] = (P.xi > 0) ? 4.0 * std::cos(sides[k]->theta_deg * M_PI / 180.0) / P.xi : 0.0;
+        d.cos_adv[k] = std::cos(sides[k]->theta_adv_deg * M_PI / 180.0);
+        d.cos_rec[k] = std::cos(sides[k]->theta_rec_deg * M_PI / 180.0);
     }
     d.zero_solid_velocity = P.zero_solid_velocity ? 1 : 0;
     d.axi = N.axisymmetric ? 1 : 0;
@@ -123,6 +127,7 @@ DomainDesc make_desc(const eulbfs_grid& g, const eulbfs_props& P, const eulbfs_b
     d.Tl = P.Tl;
     d.beta = P.sigma > 0 ? 12.0 * P.sigma / P.xi : 0.0;   // Sec. 2.3.1
     d.kappa = 1.5 * P.xi * P.sigma;
+    d.four_over_xi = P.xi > 0 ? 4.0 / P.xi : 0.0;
     d.tau_g = P.tau_g;
     d.Qg = P.Mc / ((P.tau_g - 0.5) * kDtStream);         // M_c = (tau_g - 0.5) Q_g dt_s
     d.Cref = 0.5 * (P.s.cp + P.l.cp);                    // Sec. 2.1.2

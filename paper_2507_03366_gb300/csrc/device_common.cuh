@@ -9,7 +9,8 @@
 
 namespace eulbfs {
 
-enum { BC_PERIODIC = 0, BC_DIRICHLET_T, BC_ADIABATIC, BC_NOSLIP, BC_SYMMETRY, BC_OUTLET, BC_NOFLUX, BC_WETTING };
+enum { BC_PERIODIC = 0, BC_DIRICHLET_T, BC_ADIABATIC, BC_NOSLIP, BC_SYMMETRY, BC_OUTLET, BC_NOFLUX, BC_WETTING,
+       BC_WETTING_HYST };
 
 template <class R> struct Prec;
 template <> struct Prec<double> { static constexpr int NP = 5; };
@@ -107,8 +108,58 @@ __device__ __forceinline__ void map_axis(int g, int n, int per, int lo_side, int
 template <class R>
 struct Prim { R T, Fl, cp, rho, lam, mu, p, u, v, C; };
 
+// Phase field C = C_hi + C_lo of cell c of a state buffer.
+__device__ __forceinline__ double load_C(const double* b, long long P, long long c) { return b[4 * P + c]; }
+__device__ __forceinline__ float load_C(const float* b, long long P, long long c) { return b[5 * P + c] + b[6 * P + c]; }
+
+// Wetting coefficient 4 cos(theta) / xi of the wall position t of `side`
+// (the row of an x side, the column of a y side; clamped into the domain or
+// wrapped on a periodic axis).  WETTING: the fixed angle.  WETTING_HYST
+// (contact-angle hysteresis): the apparent angle of the two wall layers,
+// cos = dC/dn_out / |grad C| with dC/dn_out = C_0 - C_1 and the tangential
+// central difference along layer 0 (one-sided at a walled end), clamped to
+// [cos theta_adv, cos theta_rec]; the fixed angle where the wall cell carries
+// no interface (C_0 (1 - C_0) < 1e-3: there the direction of grad C is
+// round-off and the wetting correction, which scales with C (1 - C), is
+// negligible).
 template <class R>
-__device__ __forceinline__ void apply_ghost(const Consts<R>& K, int side, int k, bool x_normal, Prim<R>& q) {
+__device__ __forceinline__ R wall_wetting(const Consts<R>& K, const R* in, int side, int t) {
+    if (K.bc_c[side] != BC_WETTING_HYST) return K.wet[side];
+    const bool xs = side < 2;
+    const int n = xs ? K.ny : K.nx, m = xs ? K.nx : K.ny;
+    const int per = xs ? K.per_y : K.per_x;
+    int tc, tp, tm;
+    if (per) {
+        tc = ((t % n) + n) % n;
+        tp = tc + 1 == n ? 0 : tc + 1;
+        tm = tc == 0 ? n - 1 : tc - 1;
+    } else {
+        tc = t < 0 ? 0 : (t > n - 1 ? n - 1 : t);
+        tp = tc + 1 > n - 1 ? n - 1 : tc + 1;
+        tm = tc - 1 < 0 ? 0 : tc - 1;
+    }
+    const int l0 = (side == XLO || side == YLO) ? 0 : m - 1;
+    const int l1 = (side == XLO || side == YLO) ? 1 : m - 2;
+    auto at = [&](int layer, int tt) -> R {
+        const long long c = xs ? (long long)tt * K.nx + layer : (long long)layer * K.nx + tt;
+        return load_C(in, K.plane, c);
+    };
+    const R c0 = at(l0, tc);
+    if (!(c0 * (R(1) - c0) >= R(1e-3))) return K.wet[side];
+    const R dn = c0 - at(l1, tc);
+    const R dd = at(l0, tp) - at(l0, tm);
+    const R dt = per ? R(0.5) * dd : wdiv(dd, (R)(tp - tm));
+    const R g = sqrt(dn * dn + dt * dt);
+    if (!(g > R(0))) return K.wet[side];
+    R c = wdiv(dn, g);
+    c = c < K.cos_adv[side] ? K.cos_adv[side] : (c > K.cos_rec[side] ? K.cos_rec[side] : c);
+    return K.four_over_xi * c;
+}
+
+// Ghost layer k of `side` from the mirror cell's values; wet = the side's
+// wetting coefficient at this wall position (wall_wetting).
+template <class R>
+__device__ __forceinline__ void apply_ghost(const Consts<R>& K, int side, int k, bool x_normal, R wet, Prim<R>& q) {
     if (K.bc_t[side] == BC_DIRICHLET_T) q.T = R(2) * K.Tw[side] - q.T;
     const int f = K.bc_f[side];
     if (f == BC_OUTLET) q.p = -q.p;
@@ -116,7 +167,8 @@ __device__ __forceinline__ void apply_ghost(const Consts<R>& K, int side, int k,
     R& ut = x_normal ? q.v : q.u;
     if (f == BC_NOSLIP) { un = -un; ut = -ut; }
     else if (f == BC_SYMMETRY) { un = -un; }
-    if (K.bc_c[side] == BC_WETTING) q.C = q.C + R(2 * k - 1) * K.wet[side] * q.C * (R(1) - q.C);
+    if (K.bc_c[side] == BC_WETTING || K.bc_c[side] == BC_WETTING_HYST)
+        q.C = q.C + R(2 * k - 1) * wet * q.C * (R(1) - q.C);
 }
 
 template <class R>

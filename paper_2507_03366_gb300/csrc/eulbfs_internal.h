@@ -23,6 +23,8 @@ struct DomainDesc {
     int axi;                 // 1: axisymmetric (r, z), x = r with the axis at x = 0
     double Tw[4];            // wall temperature per side (Dirichlet)
     double wet[4];           // 4 cos(theta) / xi per side (wetting)
+    double cos_adv[4], cos_rec[4];   // hysteresis window per side (WETTING_HYST)
+    double four_over_xi;
     double rho[3], mu[3], lam[3], cp[3];   // solid, liquid, gas
     double L, Ts, Tl;
     double beta, kappa;      // double-well and gradient coefficients (Sec. 2.3.1)
@@ -48,7 +50,8 @@ struct Consts {
     R rho[3], mu[3], lam[3], cp[3];
     R L, Ts, Tl, beta, kappa, Qg, tau_g, Cref, kv, gx, gy, dt;
     R six_over_Cref, inv_dt;   // 6 / C_ref = 1 / (C_ref cs^2 dt_s), 1 / dt
-    R Tw[4], wet[4];
+    R Tw[4], wet[4], cos_adv[4], cos_rec[4];
+    R four_over_xi;
     int nx, ny, per_x, per_y, zsv, axi;
     int bc_t[4], bc_f[4], bc_c[4];
     long long plane;
@@ -67,9 +70,11 @@ __host__ __device__ inline void fill_consts(const DomainDesc& d, Consts<R>& K) {
     K.Qg = (R)d.Qg; K.tau_g = (R)d.tau_g; K.Cref = (R)d.Cref; K.kv = (R)d.kv;
     K.gx = (R)d.gx; K.gy = (R)d.gy; K.dt = (R)d.dt;
     K.six_over_Cref = (R)(6.0 / d.Cref);
+    K.four_over_xi = (R)d.four_over_xi;
     K.inv_dt = (R)(1.0 / d.dt);
     for (int k = 0; k < 4; ++k) {
         K.Tw[k] = (R)d.Tw[k]; K.wet[k] = (R)d.wet[k];
+        K.cos_adv[k] = (R)d.cos_adv[k]; K.cos_rec[k] = (R)d.cos_rec[k];
         K.bc_t[k] = d.bc_t[k]; K.bc_f[k] = d.bc_f[k]; K.bc_c[k] = d.bc_c[k];
     }
     K.nx = d.nx; K.ny = d.ny; K.per_x = d.per_x; K.per_y = d.per_y;

@@ -85,8 +85,10 @@ __device__ __forceinline__ void load_rows(Smem<R>& S, const R* in, int x0, int r
         map_axis(gy, K.ny, K.per_y, YLO, sy, ky, sdy);
         const SV<R> w = load_state(in, K.plane, (long long)sy * K.nx + sx);
         Prim<R> q = derive(K, w);
-        if (kx) apply_ghost(K, sdx, kx, true, q);    // x sides first, then y (corners)
-        if (ky) apply_ghost(K, sdy, ky, false, q);
+        // x sides first, then y (corners); an x ghost takes the wetting of its
+        // (interior) row, a y ghost that of its column
+        if (kx) apply_ghost(K, sdx, kx, true, wall_wetting(K, in, sdx, sy), q);
+        if (ky) apply_ghost(K, sdy, ky, false, wall_wetting(K, in, sdy, gx), q);
         store_prim(S, slot(gy), cc, q);
     }
 }
@@ -95,11 +97,11 @@ __device__ __forceinline__ void load_rows(Smem<R>& S, const R* in, int x0, int r
 // (column gx of the domain) with the y-neighbours at sN, sS.  The Laplacian
 // is the 5-point one, or in an axisymmetric domain the conservative
 // (1/r) d/dr (r dC/dr) + d2C/dz2 with faces at r = gx and gx + 1.
-template <class R>
+template <class R, bool AXI>
 __device__ __forceinline__ R chem_potential(const Consts<R>& K, const R* C, int s0, int sN, int sS, int gx) {
     const R c = C[s0];
     R lap;
-    if (K.axi) {
+    if (AXI) {
         const R rw = (R)gx, re = rw + R(1);
         lap = wdiv(re * (C[s0 + 1] - c) - rw * (c - C[s0 - 1]), rw + R(0.5)) + (C[sN] + C[sS] - R(2) * c);
     } else {
@@ -112,7 +114,7 @@ __device__ __forceinline__ R chem_potential(const Consts<R>& K, const R* C, int 
 // (layer 1 or 2) evaluates mu_c at its mirror cell, which equals mirroring
 // the interior value; deeper layers are never read by a face of the strip
 // and get 0.
-template <class R>
+template <class R, bool AXI>
 __device__ __forceinline__ void muc_rows(Smem<R>& S, int x0, int r0, int nrows) {
     const Consts<R>& K = S.K;
     constexpr int NC = RW - 2;
@@ -125,7 +127,7 @@ __device__ __forceinline__ void muc_rows(Smem<R>& S, int x0, int r0, int nrows) 
             const int gy = r0 + rr;
             const int s0 = slot(gy) * RW + cc;
             S.P[F_MUC][slot(gy)][cc] =
-                chem_potential(K, C, s0, slot(gy + 1) * RW + cc, slot(gy - 1) * RW + cc, x0 + cc - kHalo);
+                chem_potential<R, AXI>(K, C, s0, slot(gy + 1) * RW + cc, slot(gy - 1) * RW + cc, x0 + cc - kHalo);
         }
         return;
     }
@@ -143,7 +145,7 @@ __device__ __forceinline__ void muc_rows(Smem<R>& S, int x0, int r0, int nrows) 
         }
         R mu = R(0);
         if (!deep)
-            mu = chem_potential(K, C, slot(my) * RW + mc, slot(my + 1) * RW + mc, slot(my - 1) * RW + mc,
+            mu = chem_potential<R, AXI>(K, C, slot(my) * RW + mc, slot(my + 1) * RW + mc, slot(my - 1) * RW + mc,
                                 x0 + mc - kHalo);
         S.P[F_MUC][slot(gy)][cc] = mu;
     }
@@ -222,7 +224,7 @@ __device__ __forceinline__ R face_value(const R* f, const FaceIdx& x) {
 // w_a over dt_s.  Of the fluxes only the normal momentum flux changes, by
 // cs^2 dt_s (-rho_f cs^2 u_r / r) = -rho_f u_r / (18 r) with the face values;
 // inv_r = 1 / r of the face (0 on the axis, where the face area is zero).
-template <class R>
+template <class R, bool AXI>
 __device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const R* P, const FaceIdx& x, int fUn, int fUt,
                                                  bool normal_is_r, R inv_r) {
     R un[9], ut[9], rr[9], CC[9];
@@ -319,14 +321,14 @@ __device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const R* P,
     F.Fmt = (R(1) - tf) * cs2 * rho_f * unf * utf + tf * (Snt_p + rho_f * Snt_q);
     F.Fc = (R(1) - tg) * Cf * unf + tg * Sg;     // Eq. 44, 46
     F.un = unf;
-    if (K.axi) F.Fmn += R(-1.0 / 18.0) * rho_f * (normal_is_r ? un[0] : ut[0]) * inv_r;
+    if (AXI) F.Fmn += R(-1.0 / 18.0) * rho_f * (normal_is_r ? un[0] : ut[0]) * inv_r;
     return F;
 }
 
 // Step 3, x-faces of ring row r: lane l computes the face between columns
 // l+2 and l+3 (cells x0+l-1 and x0+l), at x = x0 + l.  In an axisymmetric
 // domain the stored fluxes are multiplied by the face area r_f = x0 + l.
-template <class R>
+template <class R, bool AXI>
 __device__ __forceinline__ void x_face(Smem<R>& S, int x0, int r, int row_in_chunk, int lane) {
     FaceIdx x;
     const int cL = lane + 2;
@@ -339,9 +341,9 @@ __device__ __forceinline__ void x_face(Smem<R>& S, int x0, int r, int row_in_chu
     x.Rp = x.Lp + 1;
     x.Rm = x.Lm + 1;
     const int gf = x0 + lane;
-    const R rf = S.K.axi ? (R)gf : R(1);
-    FaceFlux<R> F = face_flux(S.K, &S.P[0][0][0], x, F_U, F_V, true, gf > 0 ? wdiv(R(1), rf) : R(0));
-    if (S.K.axi) {
+    const R rf = AXI ? (R)gf : R(1);
+    FaceFlux<R> F = face_flux<R, AXI>(S.K, &S.P[0][0][0], x, F_U, F_V, true, (AXI && gf > 0) ? wdiv(R(1), rf) : R(0));
+    if (AXI) {
         F.Fh *= rf; F.Fp *= rf; F.Fmn *= rf; F.Fmt *= rf; F.Fc *= rf; F.un *= rf;
     }
     S.XF[0][row_in_chunk][lane] = F.Fh;
@@ -354,7 +356,7 @@ __device__ __forceinline__ void x_face(Smem<R>& S, int x0, int r, int row_in_chu
 
 // Step 3, y-faces of face row r (between rows r-1 and r), lane l < 31 at
 // column l+3 (cell x0 + l, radius x0 + l + 1/2 in an axisymmetric domain).
-template <class R>
+template <class R, bool AXI>
 __device__ __forceinline__ void y_face(Smem<R>& S, int x0, int r, int lane) {
     FaceIdx x;
     const int c = lane + kHalo;
@@ -366,8 +368,8 @@ __device__ __forceinline__ void y_face(Smem<R>& S, int x0, int r, int lane) {
     x.Lm = x.L - 1;
     x.Rp = x.R + 1;
     x.Rm = x.R - 1;
-    const R inv_r = S.K.axi ? wdiv(R(1), (R)(x0 + lane) + R(0.5)) : R(0);
-    const FaceFlux<R> F = face_flux(S.K, &S.P[0][0][0], x, F_V, F_U, false, inv_r);
+    const R inv_r = AXI ? wdiv(R(1), (R)(x0 + lane) + R(0.5)) : R(0);
+    const FaceFlux<R> F = face_flux<R, AXI>(S.K, &S.P[0][0][0], x, F_V, F_U, false, inv_r);
     const int s = slot(r);
     S.YF[0][s][lane] = F.Fh;
     S.YF[1][s][lane] = F.Fp;
@@ -378,7 +380,7 @@ __device__ __forceinline__ void y_face(Smem<R>& S, int x0, int r, int lane) {
 }
 
 // Step 4 for the cell (r, x0 + lane).
-template <class R>
+template <class R, bool AXI>
 __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r, int row_in_chunk, int lane,
                                             int* flag) {
     const Consts<R>& K = S.K;
@@ -389,14 +391,15 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
     const int sr = slot(r), sn = slot(r + 1);
     // Eq. 52; axisymmetric: the x-face fluxes carry their areas r_f, divided
     // here by the cell volume r_i = gx + 1/2 (per radian)
-    const R irc = K.axi ? wdiv(R(1), (R)gx + R(0.5)) : R(1);
+    const R irc = AXI ? wdiv(R(1), (R)gx + R(0.5)) : R(1);
     R Rk[5];
 #pragma unroll
-    for (int k = 0; k < 5; ++k)
-        Rk[k] = -((S.XF[k][row_in_chunk][lane + 1] - S.XF[k][row_in_chunk][lane]) * irc +
-                  (S.YF[k][sn][lane] - S.YF[k][sr][lane]));
-    const R divu =
-        (S.XF[5][row_in_chunk][lane + 1] - S.XF[5][row_in_chunk][lane]) * irc + (S.YF[5][sn][lane] - S.YF[5][sr][lane]);
+    for (int k = 0; k < 5; ++k) {
+        const R dx = S.XF[k][row_in_chunk][lane + 1] - S.XF[k][row_in_chunk][lane];
+        Rk[k] = -((AXI ? dx * irc : dx) + (S.YF[k][sn][lane] - S.YF[k][sr][lane]));
+    }
+    const R dxu = S.XF[5][row_in_chunk][lane + 1] - S.XF[5][row_in_chunk][lane];
+    const R divu = (AXI ? dxu * irc : dxu) + (S.YF[5][sn][lane] - S.YF[5][sr][lane]);
     const R divF1 = -Rk[1];   // div(rho cs^2 u), the pressure-flux divergence
 
     const R* P = &S.P[0][0][0];
@@ -423,7 +426,7 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
     Rk[2] += cs2 * (-Fl * C * dmx + rho * K.gx - rho * u * D);         // row 3 (R13)
     Rk[3] += cs2 * (-Fl * C * dmy + rho * K.gy - rho * v * D);         // row 4
     Rk[4] += C * K.kv * D;                                             // row 5 (R12)
-    if (K.axi)   // hoop stress Pi_thetatheta / r with the pressure advanced over dt_s (reading R24)
+    if (AXI)   // hoop stress Pi_thetatheta / r with the pressure advanced over dt_s (reading R24)
         Rk[2] += cs2 * (P[F_P * FS + q] - R(0.5) * divF1 - R(2) * P[F_MU * FS + q] * u * irc) * irc;
 
     const R* in = reinterpret_cast<const R*>(K.st[stage]);
@@ -473,6 +476,40 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
     store_state(reinterpret_cast<R*>(K.st[stage == 2 ? 0 : stage + 1]), K.plane, c, o);
 }
 
+// One work item: the strip segment [x0, x0 + 31) x [y0, y1) of the domain
+// whose constants are in S.K (planar or axisymmetric, fixed per domain).
+template <class R, bool AXI>
+__device__ __forceinline__ void sweep_item(Smem<R>& S, const StageLaunch& a, int x0, int y0, int y1) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const R* in = reinterpret_cast<const R*>(S.K.st[a.stage]);
+
+    // prologue: rows y0-3 .. y0+2, mu_c of rows y0-2 .. y0+1, y-face row y0
+    load_rows(S, in, x0, y0 - kHalo, 2 * kHalo);
+    __syncthreads();
+    muc_rows<R, AXI>(S, x0, y0 - 2, 4);
+    __syncthreads();
+    if (warp == 0 && lane < kStripX) y_face<R, AXI>(S, x0, y0, lane);
+    // (the first chunk writes other ring rows: no barrier needed here)
+
+    for (int j0 = y0; j0 < y1; j0 += kChunk) {
+        load_rows(S, in, x0, j0 + kHalo, kChunk);     // rows j0+3 .. j0+10
+        __syncthreads();
+        muc_rows<R, AXI>(S, x0, j0 + 2, kChunk);      // rows j0+2 .. j0+9
+        __syncthreads();
+        // one face at a time per thread (x then y) keeps register use low
+#pragma unroll 1
+        for (int k = 0; k < 2; ++k) {
+            if (k == 0) x_face<R, AXI>(S, x0, j0 + warp, warp, lane);
+            else if (lane < kStripX) y_face<R, AXI>(S, x0, j0 + 1 + warp, lane);
+        }
+        __syncthreads();
+        const int r = j0 + warp;
+        if (r < y1 && lane < kStripX && x0 + lane < S.K.nx)
+            cell_update<R, AXI>(S, a.stage, x0, r, warp, lane, a.flag);
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 template <class R>
@@ -480,7 +517,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) stage_kernel(Stage
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<R>& S = *reinterpret_cast<Smem<R>*>(smem_raw);
     __shared__ int cur_domain;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     if (tid == 0) cur_domain = -1;
     __syncthreads();
     const Consts<R>* consts = static_cast<const Consts<R>*>(a.consts);
@@ -499,32 +536,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) stage_kernel(Stage
         const int x0 = item.y * kStripX;
         const int y0 = item.z * a.seg;
         const int y1 = min(y0 + a.seg, S.K.ny);
-        const R* in = reinterpret_cast<const R*>(S.K.st[a.stage]);
-
-        // prologue: rows y0-3 .. y0+2, mu_c of rows y0-2 .. y0+1, y-face row y0
-        load_rows(S, in, x0, y0 - kHalo, 2 * kHalo);
-        __syncthreads();
-        muc_rows(S, x0, y0 - 2, 4);
-        __syncthreads();
-        if (warp == 0 && lane < kStripX) y_face(S, x0, y0, lane);
-        // (the first chunk writes other ring rows: no barrier needed here)
-
-        for (int j0 = y0; j0 < y1; j0 += kChunk) {
-            load_rows(S, in, x0, j0 + kHalo, kChunk);     // rows j0+3 .. j0+10
-            __syncthreads();
-            muc_rows(S, x0, j0 + 2, kChunk);              // rows j0+2 .. j0+9
-            __syncthreads();
-            // one face at a time per thread (x then y) keeps register use low
-#pragma unroll 1
-            for (int k = 0; k < 2; ++k) {
-                if (k == 0) x_face(S, x0, j0 + warp, warp, lane);
-                else if (lane < kStripX) y_face(S, x0, j0 + 1 + warp, lane);
-            }
-            __syncthreads();
-            const int r = j0 + warp;
-            if (r < y1 && lane < kStripX && x0 + lane < S.K.nx) cell_update(S, a.stage, x0, r, warp, lane, a.flag);
-            __syncthreads();
-        }
+        if (S.K.axi) sweep_item<R, true>(S, a, x0, y0, y1);
+        else sweep_item<R, false>(S, a, x0, y0, y1);
     }
 }
 

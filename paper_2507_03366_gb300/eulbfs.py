@@ -44,7 +44,7 @@ class Props(ct.Structure):
 
 class Side(ct.Structure):
     _fields_ = [("thermal", ct.c_int), ("flow", ct.c_int), ("phase", ct.c_int), ("Tw", ct.c_double),
-                ("theta_deg", ct.c_double)]
+                ("theta_deg", ct.c_double), ("theta_adv_deg", ct.c_double), ("theta_rec_deg", ct.c_double)]
 
 
 class BC(ct.Structure):
@@ -148,7 +148,8 @@ def _props(p) -> Props:
 
 
 def _bc(b) -> BC:
-    sd = lambda q: Side(q.thermal, q.flow, q.phase, q.Tw, q.theta_deg)  # noqa: E731
+    sd = lambda q: Side(q.thermal, q.flow, q.phase, q.Tw, q.theta_deg,  # noqa: E731
+                        getattr(q, "theta_adv_deg", q.theta_deg), getattr(q, "theta_rec_deg", q.theta_deg))
     return BC(sd(b.xlo), sd(b.xhi), sd(b.ylo), sd(b.yhi))
 
 

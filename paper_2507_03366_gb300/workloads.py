@@ -89,6 +89,9 @@ class Case:
     init: Dict[str, np.ndarray] = field(repr=False)
     dt_stream: float = 0.5
     axisymmetric: int = 0      # 1: x is the radius r (axis at x = 0), y the axial z
+    dt_h: float = 0.0          # streaming steps of the h, f, g distributions (0: dt_stream)
+    dt_f: float = 0.0
+    dt_g: float = 0.0
 
     @property
     def cells(self) -> int:
@@ -220,7 +223,7 @@ def film(n: int = 512, seed: int = 3, dt: float = 0.5, height: float = 0.3,
 def droplet(side: int, theta_deg: float = 90.0, St: float = 0.2, rho_sl: float = 0.917,
             Tw: float = -0.5, dt: float = 0.5, name: str | None = None,
             impact_speed: float = 0.0, We: float | None = None, Re: float | None = None,
-            axisymmetric: bool = False) -> Case:
+            axisymmetric: bool = False, hysteresis: tuple | None = None) -> Case:
     """Half droplet of radius 0.25*side on the plate y = 0 with its axis at
     x = 0: a planar 2-D drop with a symmetry plane there, or with
     axisymmetric=True the drop of revolution in (r, z) (reading R18).
@@ -228,7 +231,9 @@ def droplet(side: int, theta_deg: float = 90.0, St: float = 0.2, rho_sl: float =
     With impact_speed U > 0 the drop is released at rest 0.1*side above the
     plate under gravity g = U^2 / (2 gap), reaching U at contact (an impulsive
     start would send pressure waves through the light gas), and We, Re are
-    defined with U and the diameter D = 2R."""
+    defined with U and the diameter D = 2R.  hysteresis = (theta_adv,
+    theta_rec) makes the plate a hysteresis wetting wall (reading R25) with
+    theta_deg as its equilibrium angle."""
     Tm = 0.0
     R = 0.25 * side
     rl, rg, rs = 1.0, 1e-3, rho_sl
@@ -254,7 +259,8 @@ def droplet(side: int, theta_deg: float = 90.0, St: float = 0.2, rho_sl: float =
     nu_max = max(mu_l / rl, (mu_l / 100.0) / rg)
     dt = min(dt, 0.1 / nu_max, 1.5 / (64.0 * props.Mc * 1.5 * props.xi * props.sigma))
     bc = BC(xlo=_wall(ADIABATIC, SYMMETRY, NOFLUX), xhi=_wall(ADIABATIC, NOSLIP, NOFLUX),
-            ylo=_wall(DIRICHLET_T, NOSLIP, WETTING, Tw=Tw, theta=theta_deg),
+            ylo=_wall(DIRICHLET_T, NOSLIP, WETTING, Tw=Tw, theta=theta_deg) if hysteresis is None else
+            Side(DIRICHLET_T, NOSLIP, WETTING_HYST, Tw, theta_deg, hysteresis[0], hysteresis[1]),
             yhi=_wall(ADIABATIC, NOSLIP, NOFLUX))
     x = np.arange(side) + 0.5
     y = np.arange(side) + 0.5
