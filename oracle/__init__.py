@@ -62,7 +62,8 @@ class BC(ct.Structure):
 
 
 class Numerics(ct.Structure):
-    _fields_ = [("dt", ct.c_double), ("dt_stream", ct.c_double), ("axisymmetric", ct.c_int)]
+    _fields_ = [("dt", ct.c_double), ("dt_stream", ct.c_double), ("axisymmetric", ct.c_int),
+                ("dt_h", ct.c_double), ("dt_f", ct.c_double), ("dt_g", ct.c_double)]
 
 
 _DP = ct.POINTER(ct.c_double)
@@ -174,7 +175,8 @@ class OracleSolver:
                       for k in ("T", "Fl", "C", "u", "v", "p")}
         init = Init(*[_ptr(self._keep[k]) for k in ("T", "Fl", "C", "u", "v", "p")])
         P, B = props_struct(case.props), bc_struct(case.bc)
-        N = Numerics(case.dt, case.dt_stream, int(getattr(case, "axisymmetric", 0)))
+        N = Numerics(case.dt, case.dt_stream, int(getattr(case, "axisymmetric", 0)),
+                     *[float(getattr(case, k, 0.0) or 0.0) for k in ("dt_h", "dt_f", "dt_g")])
         err = ct.create_string_buffer(256)
         h = lib().or_create(case.nx, case.ny, ct.byref(P), ct.byref(B), ct.byref(N), ct.byref(init), err)
         if not h:

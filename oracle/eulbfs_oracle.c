@@ -47,6 +47,7 @@ struct or_solver {
     or_bc B;
     or_numerics N;
     double Cref, beta, kappa, Qg;
+    double dth, dtf, dtg;  /* streaming steps of h, f, g (R26) */
     double* W[5];          /* conserved state (Eq. 49) */
     double* Fsp;           /* F_s at the previous step (R14) */
     double* dFs;           /* (F_s^n - F_s^{n-1}) / dt, fixed during one step */
@@ -341,22 +342,12 @@ static double recon(const or_solver* s, int f, int ci, int cj, double x, double 
 /* Face flux: Sec. 2.5 steps (2)-(4) and Eq. 53.                        */
 /* ------------------------------------------------------------------ */
 
-static void face_flux(const or_solver* s, int dir, int i, int j, double out[6]) {
-    const double dts = s->N.dt_stream;
-    double xf, yf, nxv, nyv;
-    int Li, Lj, Ri, Rj;
-    if (dir == 0) {
-        xf = i; yf = j + 0.5; nxv = 1.0; nyv = 0.0;
-        Li = i - 1; Lj = j; Ri = i; Rj = j;
-    } else {
-        xf = i + 0.5; yf = j; nxv = 0.0; nyv = 1.0;
-        Li = i; Lj = j - 1; Ri = i; Rj = j;
-    }
-
-    /* step (2): macroscopic variables at x_f - e_alpha dt_s by Eq. 54.
-     * The point belongs to the cell on whose side of the face it lies; on the
-     * face itself the values are the mean of the two reconstructions (R7). */
-    double q[9][NPRIM];
+/* step (2): macroscopic variables at the points x_f - e_alpha dts of the
+ * face (xf, yf) with normal (nxv, nyv) by Eq. 54.  The point belongs to the
+ * cell on whose side of the face it lies; on the face itself the values are
+ * the mean of the two reconstructions (R7). */
+static void surrounding(const or_solver* s, double xf, double yf, double nxv, double nyv, int Li, int Lj,
+                        int Ri, int Rj, double dts, double q[9][NPRIM]) {
     for (int a = 0; a < 9; ++a) {
         const double sx = xf - EX[a] * dts, sy = yf - EY[a] * dts;
         const double off = (sx - xf) * nxv + (sy - yf) * nyv;
@@ -370,6 +361,30 @@ static void face_flux(const or_solver* s, int dir, int i, int j, double out[6]) 
                 q[a][f] = 0.5 * (recon(s, f, Li, Lj, sx, sy) + recon(s, f, Ri, Rj, sx, sy));
         }
     }
+}
+
+static void face_flux(const or_solver* s, int dir, int i, int j, double out[6]) {
+    const double dts = s->dtf;   /* flow streaming step: R24 terms */
+    double xf, yf, nxv, nyv;
+    int Li, Lj, Ri, Rj;
+    if (dir == 0) {
+        xf = i; yf = j + 0.5; nxv = 1.0; nyv = 0.0;
+        Li = i - 1; Lj = j; Ri = i; Rj = j;
+    } else {
+        xf = i + 0.5; yf = j; nxv = 0.0; nyv = 1.0;
+        Li = i; Lj = j - 1; Ri = i; Rj = j;
+    }
+
+    /* Reading R26: each distribution streams over its own step, so h, f and
+     * g take their surrounding points at x_f - e_alpha dt_h, dt_f, dt_g.  The
+     * alpha = 0 point is the face itself for all three. */
+    double qh[9][NPRIM], qf[9][NPRIM], qg[9][NPRIM];
+    surrounding(s, xf, yf, nxv, nyv, Li, Lj, Ri, Rj, s->dtf, qf);
+    if (s->dth == s->dtf) memcpy(qh, qf, sizeof(qh));
+    else surrounding(s, xf, yf, nxv, nyv, Li, Lj, Ri, Rj, s->dth, qh);
+    if (s->dtg == s->dtf) memcpy(qg, qf, sizeof(qg));
+    else surrounding(s, xf, yf, nxv, nyv, Li, Lj, Ri, Rj, s->dtg, qg);
+    double (*q)[NPRIM] = qf;
 
     /* face values at the current time: mean of the L/R reconstructions at
      * the face (text under Eq. 54), i.e. the alpha = 0 point (R9). */
@@ -379,10 +394,10 @@ static void face_flux(const or_solver* s, int dir, int i, int j, double out[6]) 
     /* step (2): surrounding equilibria, Eq. 9, 29, 33, 42 */
     double heqs[9], feqs[9], feqms[9], geqs[9];
     for (int a = 0; a < 9; ++a) {
-        heqs[a] = or_heq(a, q[a][P_H], q[a][P_T], q[a][P_CP], s->Cref, q[a][P_U], q[a][P_V]);
-        feqs[a] = or_feq(a, q[a][P_P], q[a][P_RHO], q[a][P_U], q[a][P_V]);
-        feqms[a] = or_feqm(a, q[a][P_P], rho_f, q[a][P_U], q[a][P_V]);
-        geqs[a] = or_geq(a, q[a][P_C], q[a][P_MUC], s->Qg, q[a][P_U], q[a][P_V]);
+        heqs[a] = or_heq(a, qh[a][P_H], qh[a][P_T], qh[a][P_CP], s->Cref, qh[a][P_U], qh[a][P_V]);
+        feqs[a] = or_feq(a, qf[a][P_P], qf[a][P_RHO], qf[a][P_U], qf[a][P_V]);
+        feqms[a] = or_feqm(a, qf[a][P_P], rho_f, qf[a][P_U], qf[a][P_V]);
+        geqs[a] = or_geq(a, qg[a][P_C], qg[a][P_MUC], s->Qg, qg[a][P_U], qg[a][P_V]);
     }
     if (s->N.axisymmetric && xf > 0.0) {
         /* Axisymmetric runs (reading R24): the pressure equation has the
@@ -410,8 +425,8 @@ static void face_flux(const or_solver* s, int dir, int i, int j, double out[6]) 
     const double uf = mxf / (rho_f * CS2), vf = myf / (rho_f * CS2);
 
     /* relaxation parameters with the face properties (Sec. 2.1.2, 2.2.3, 2.3.2) */
-    const double tau_h = 0.5 + lamf / (rho_f * s->Cref * CS2 * dts);
-    const double tau_f = 0.5 + muf / (rho_f * CS2 * dts);
+    const double tau_h = 0.5 + lamf / (rho_f * s->Cref * CS2 * s->dth);
+    const double tau_f = 0.5 + muf / (rho_f * CS2 * s->dtf);
     const double tau_g = s->P.tau_g;
 
     /* steps (3)-(4) and Eq. 53 */
@@ -492,7 +507,7 @@ static void residual(or_solver* s, double* const W[5], double* const R[5]) {
                  * (reading R24): the pressure advanced over dt_s like the face
                  * pressures, p - dt_s div(rho cs^2 u), and the viscous -2 mu u_r / r */
                 const double rc = i + 0.5;
-                FE[2] += CS2 * (s->prim[P_P][q] - s->N.dt_stream * divF[1] -
+                FE[2] += CS2 * (s->prim[P_P][q] - s->dtf * divF[1] -
                                 2.0 * s->prim[P_MU][q] * u / rc) / rc;
             }
             for (int k = 0; k < 5; ++k) R[k][c] = -divF[k] + FE[k];
@@ -557,8 +572,11 @@ or_solver* or_create(int nx, int ny, const or_props* P, const or_bc* B, const or
         return NULL;
     }
     if (P->sigma > 0 && !(P->xi > 0)) { bad(err, "xi must be > 0"); return NULL; }
-    if (!(N->dt > 0 && N->dt_stream > 0 && N->dt_stream <= 0.5)) {
-        bad(err, "need dt > 0 and 0 < dt_stream <= 0.5");
+    const double dsx[3] = {N->dt_h, N->dt_f, N->dt_g};
+    int dts_ok = N->dt > 0 && N->dt_stream > 0 && N->dt_stream <= 0.5;
+    for (int k = 0; k < 3; ++k) dts_ok &= dsx[k] == 0.0 || (dsx[k] > 0.0 && dsx[k] <= 0.5);
+    if (!dts_ok) {
+        bad(err, "need dt > 0 and streaming steps in (0, 0.5]");
         return NULL;
     }
     if (!I || !I->T || !I->C) { bad(err, "initial T and C are required"); return NULL; }
@@ -574,7 +592,10 @@ or_solver* or_create(int nx, int ny, const or_props* P, const or_bc* B, const or
     s->Cref = 0.5 * (P->s.cp + P->l.cp);                 /* R16 */
     s->beta = P->sigma > 0 ? 12.0 * P->sigma / P->xi : 0.0;   /* Sec. 2.3.1 */
     s->kappa = 1.5 * P->xi * P->sigma;
-    s->Qg = P->Mc / ((P->tau_g - 0.5) * N->dt_stream);  /* M_c = (tau_g - 0.5) Q_g dt_s */
+    s->dth = N->dt_h > 0 ? N->dt_h : N->dt_stream;
+    s->dtf = N->dt_f > 0 ? N->dt_f : N->dt_stream;
+    s->dtg = N->dt_g > 0 ? N->dt_g : N->dt_stream;
+    s->Qg = P->Mc / ((P->tau_g - 0.5) * s->dtg);   /* M_c = (tau_g - 0.5) Q_g dt_g */
     const size_t n = (size_t)nx * ny, np = (size_t)s->px * s->py;
     for (int k = 0; k < 5; ++k) { s->W[k] = alloc0(n); s->Wn[k] = alloc0(n); s->R[k] = alloc0(n); }
     s->Fsp = alloc0(n); s->dFs = alloc0(n);

@@ -65,6 +65,9 @@ typedef struct {
     double dt;        /* Runge-Kutta time step Delta t (Eq. 58) */
     double dt_stream; /* streaming step delta t (Sec. 2.5 step 1), 0 < dt_stream <= 0.5 */
     int axisymmetric; /* 1: x is the radius r (axis at x = 0), y the axial coordinate z */
+    /* per-distribution streaming steps of h (enthalpy), f (flow) and g (phase
+     * field), each in (0, 0.5]; 0 means dt_stream (reading R26) */
+    double dt_h, dt_f, dt_g;
 } or_numerics;
 
 /* Initial primitive fields, host arrays of nx*ny doubles, copied at create.

@@ -16,6 +16,7 @@ SRC = os.path.join(ROOT, "oracle", "eulbfs_oracle.c")
 PINS = "tests/test_oracle_pins.py::"
 AXI = "tests/test_oracle_axisymmetric.py::"
 HYS = "tests/test_oracle_hysteresis.py::"
+STR = "tests/test_oracle_streaming.py::"
 
 # (name, original text, planted text, pin that must fail)
 MUTATIONS = [
@@ -89,6 +90,17 @@ MUTATIONS = [
      HYS + "test_contact_line_pinned_inside_window"),
     ("hysteresis_limits_swapped", "return c < lo ? lo : (c > hi ? hi : c);", "return c < hi ? hi : (c > lo ? lo : c);",
      HYS + "test_limits_act_as_static_angles_outside_window"),
+    # per-distribution streaming steps (reading R26)
+    ("streaming_h_points_from_f", "else surrounding(s, xf, yf, nxv, nyv, Li, Lj, Ri, Rj, s->dth, qh);",
+     "else surrounding(s, xf, yf, nxv, nyv, Li, Lj, Ri, Rj, s->dtf, qh);", STR + "test_conduction_flux_hand_expanded"),
+    ("streaming_g_points_from_f", "else surrounding(s, xf, yf, nxv, nyv, Li, Lj, Ri, Rj, s->dtg, qg);",
+     "else surrounding(s, xf, yf, nxv, nyv, Li, Lj, Ri, Rj, s->dtf, qg);", STR + "test_phase_field_fluxes_with_steps"),
+    ("streaming_tau_f_step", "const double tau_f = 0.5 + muf / (rho_f * CS2 * s->dtf);",
+     "const double tau_f = 0.5 + muf / (rho_f * CS2 * s->dth);", STR + "test_shear_flux_independent_of_steps"),
+    ("streaming_Qg_step", "s->Qg = P->Mc / ((P->tau_g - 0.5) * s->dtg);", "s->Qg = P->Mc / ((P->tau_g - 0.5) * s->dtf);",
+     STR + "test_phase_field_fluxes_with_steps"),
+    ("streaming_hoop_step", "FE[2] += CS2 * (s->prim[P_P][q] - s->dtf * divF[1] -",
+     "FE[2] += CS2 * (s->prim[P_P][q] - s->dth * divF[1] -", STR + "test_axisymmetric_radial_expansion_with_steps"),
 ]
 
 
