@@ -103,6 +103,13 @@ typedef struct {
      * axisymmetric mass source -rho cs^2 u_r / r in the face pressure.  The
      * xlo side must be ADIABATIC / SYMMETRY / NOFLUX (EINVAL otherwise). */
     int axisymmetric;
+    /* Streaming steps of the enthalpy (h), flow (f) and phase-field (g)
+     * distributions in lattice units (Sec. 2.5 step (1)): each takes its
+     * surrounding points at x_f - e_a dt and its relaxation time from its own
+     * step.  0 selects 0.5, where the points fall on cell centres and face
+     * midpoints (the fast path); any value must lie in (0, 0.5] (EINVAL
+     * otherwise).  Smaller steps carry less numerical dissipation. */
+    double dt_stream_h, dt_stream_f, dt_stream_g;
 } eulbfs_numerics;
 
 /* Initial primitive fields: host arrays of nx*ny doubles, copied at creation.

@@ -91,6 +91,9 @@ int validate(const eulbfs_grid& g, const eulbfs_props& P, const eulbfs_bc& B, co
     if (P.sigma > 0 && !(P.xi > 0)) return fail(EULBFS_EINVAL, "xi must be > 0 when sigma > 0");
     if (!(N.dt > 0 && std::isfinite(N.dt))) return fail(EULBFS_EINVAL, "dt must be > 0");
     if (N.axisymmetric != 0 && N.axisymmetric != 1) return fail(EULBFS_EINVAL, "axisymmetric must be 0 or 1");
+    for (double ds : {N.dt_stream_h, N.dt_stream_f, N.dt_stream_g})
+        if (!(ds == 0.0 || (ds > 0.0 && ds <= 0.5)))
+            return fail(EULBFS_EINVAL, "streaming steps must be 0 (default 0.5) or in (0, 0.5]");
     if (N.axisymmetric && !(B.xlo.thermal == EULBFS_BC_ADIABATIC && B.xlo.flow == EULBFS_BC_SYMMETRY &&
                             B.xlo.phase == EULBFS_BC_NOFLUX))
         return fail(EULBFS_EINVAL, "an axisymmetric domain needs the axis (xlo) adiabatic, symmetric and no-flux");
@@ -129,7 +132,10 @@ DomainDesc make_desc(const eulbfs_grid& g, const eulbfs_props& P, const eulbfs_b
     d.kappa = 1.5 * P.xi * P.sigma;
     d.four_over_xi = P.xi > 0 ? 4.0 / P.xi : 0.0;
     d.tau_g = P.tau_g;
-    d.Qg = P.Mc / ((P.tau_g - 0.5) * kDtStream);         // M_c = (tau_g - 0.5) Q_g dt_s
+    d.dts[0] = N.dt_stream_h > 0 ? N.dt_stream_h : kDtStream;
+    d.dts[1] = N.dt_stream_f > 0 ? N.dt_stream_f : kDtStream;
+    d.dts[2] = N.dt_stream_g > 0 ? N.dt_stream_g : kDtStream;
+    d.Qg = P.Mc / ((P.tau_g - 0.5) * d.dts[2]);          // M_c = (tau_g - 0.5) Q_g dt_g
     d.Cref = 0.5 * (P.s.cp + P.l.cp);                    // Sec. 2.1.2
     d.kv = 1.0 - P.s.rho / P.l.rho;
     d.gx = P.gx;

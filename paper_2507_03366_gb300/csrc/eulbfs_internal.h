@@ -29,6 +29,7 @@ struct DomainDesc {
     double L, Ts, Tl;
     double beta, kappa;      // double-well and gradient coefficients (Sec. 2.3.1)
     double Qg, tau_g;        // phase-field diffusion parameter and relaxation (Sec. 2.3.2)
+    double dts[3];           // streaming steps of h, f, g (0.5 unless chosen otherwise)
     double Cref;             // 0.5 (cp_s + cp_l) (Sec. 2.1.2)
     double kv;               // 1 - rho_s / rho_l
     double gx, gy;
@@ -50,9 +51,13 @@ struct Consts {
     R rho[3], mu[3], lam[3], cp[3];
     R L, Ts, Tl, beta, kappa, Qg, tau_g, Cref, kv, gx, gy, dt;
     R six_over_Cref, inv_dt;   // 6 / C_ref = 1 / (C_ref cs^2 dt_s), 1 / dt
+    R dth, dtf, dtg;           // streaming steps of h, f, g
+    R th_coef, tf_coef;        // 3 / (C_ref dt_h), 3 / dt_f: tau - 1/2 = coef x lambda (or mu) / rho
     R Tw[4], wet[4], cos_adv[4], cos_rec[4];
     R four_over_xi;
     int nx, ny, per_x, per_y, zsv, axi;
+    int gen;                   // 1: some streaming step differs from 0.5 (general face path)
+    int pad2_;
     int bc_t[4], bc_f[4], bc_c[4];
     long long plane;
     void* st[3];
@@ -71,6 +76,11 @@ __host__ __device__ inline void fill_consts(const DomainDesc& d, Consts<R>& K) {
     K.gx = (R)d.gx; K.gy = (R)d.gy; K.dt = (R)d.dt;
     K.six_over_Cref = (R)(6.0 / d.Cref);
     K.four_over_xi = (R)d.four_over_xi;
+    K.dth = (R)d.dts[0]; K.dtf = (R)d.dts[1]; K.dtg = (R)d.dts[2];
+    K.th_coef = (R)(3.0 / (d.Cref * d.dts[0]));
+    K.tf_coef = (R)(3.0 / d.dts[1]);
+    K.gen = (d.dts[0] != 0.5 || d.dts[1] != 0.5 || d.dts[2] != 0.5) ? 1 : 0;
+    K.pad2_ = 0;
     K.inv_dt = (R)(1.0 / d.dt);
     for (int k = 0; k < 4; ++k) {
         K.Tw[k] = (R)d.Tw[k]; K.wet[k] = (R)d.wet[k];

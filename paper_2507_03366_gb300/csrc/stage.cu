@@ -325,10 +325,169 @@ __device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const R* P,
     return F;
 }
 
+// ---------------------------------------------------------------------------
+// General streaming steps (reading R26): h, f and g take their surrounding
+// points at x_f - e_a dt_h, dt_f, dt_g.  A side point then lies inside its
+// cell at distance a = 1/2 - dt from the centre along n and dt along t, so
+// its value is f' -/+ (dt/2) d_t f with f' = f + a g_n (g_n the central
+// n-slope of that cell); the face points move by -/+ (dt/4)(d_t f_L + d_t f_R).
+// The closed forms of the linear parts keep their shape with f' for f and
+// dt/12, dt/36 for the t-moments; the per-point sums run once per
+// distribution on its own points.  Used only when some step differs from
+// 1/2; face_flux above is this with a = 0, dt = 1/2.
+// ---------------------------------------------------------------------------
+template <class R>
+struct RecN { R l, r, gl, gr, o0, dtl, dtr; };
+
+template <class R>
+__device__ __forceinline__ RecN<R> recn(const R* f, const FaceIdx& x) {
+    RecN<R> z;
+    z.l = f[x.L];
+    z.r = f[x.R];
+    z.gl = R(0.5) * (z.r - f[x.LL]);
+    z.gr = R(0.5) * (f[x.RR] - z.l);
+    z.o0 = R(0.5) * ((z.l + R(0.5) * z.gl) + (z.r - R(0.5) * z.gr));
+    z.dtl = f[x.Lp] - f[x.Lm];
+    z.dtr = f[x.Rp] - f[x.Rm];
+    return z;
+}
+
+// Values at the 9 points x_f - e_a dt (order as in all_points); a = 1/2 - dt.
+template <class R>
+__device__ __forceinline__ void points_dt(const RecN<R>& z, R dt, R o[9]) {
+    const R a = R(0.5) - dt, b = R(0.5) * dt;
+    const R lp = z.l + a * z.gl, rp = z.r - a * z.gr;
+    const R st = R(0.5) * b * (z.dtl + z.dtr);
+    o[0] = z.o0;
+    o[1] = lp;
+    o[2] = z.o0 - st;
+    o[3] = rp;
+    o[4] = z.o0 + st;
+    o[5] = lp - b * z.dtl;
+    o[6] = rp - b * z.dtr;
+    o[7] = rp + b * z.dtr;
+    o[8] = lp + b * z.dtl;
+}
+
+__device__ __forceinline__ int e_n(int a) { return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0); }
+__device__ __forceinline__ int e_t(int a) { return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0); }
+
+template <class R>
+__device__ __forceinline__ R e_dot(int a, R un, R ut) {
+    const int en = e_n(a), et = e_t(a);
+    return (en == 0 ? R(0) : (en > 0 ? un : -un)) + (et == 0 ? R(0) : (et > 0 ? ut : -ut));
+}
+
+template <class R, bool AXI>
+__device__ __forceinline__ FaceFlux<R> face_flux_gen(const Consts<R>& K, const R* P, const FaceIdx& x, int fUn, int fUt,
+                                                  bool normal_is_r, R inv_r) {
+    const R w0 = R(4.0 / 9.0), w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
+    const RecN<R> Un = recn(P + fUn * FS, x), Ut = recn(P + fUt * FS, x);
+    // f: points at dt_f
+    R fq0, pf_a = R(0), mn_a = R(0), mt_a = R(0), pf_d = R(0), mn_d = R(0), mt_d = R(0);
+    R qn_a = R(0), qn_d = R(0), qt_d = R(0), rho_f, unf0, utf0;
+    {
+        R un[9], ut[9], rr[9];
+        points_dt(Un, K.dtf, un);
+        points_dt(Ut, K.dtf, ut);
+        points_dt(recn(P + F_RHO * FS, x), K.dtf, rr);
+        rho_f = rr[0];
+        unf0 = un[0];
+        utf0 = ut[0];
+        fq0 = rr[0] * (R(-0.5) * (un[0] * un[0] + ut[0] * ut[0]));
+#pragma unroll
+        for (int a = 1; a < 9; ++a) {
+            const int en = e_n(a), et = e_t(a);
+            const R eu = e_dot(a, un[a], ut[a]);
+            const R q = eu + R(1.5) * eu * eu - R(0.5) * (un[a] * un[a] + ut[a] * ut[a]);
+            const R fq = rr[a] * q;
+            if (a < 5) {
+                pf_a += fq;
+                if (en != 0) { mn_a += en > 0 ? fq : -fq; qn_a += q; }
+                if (et != 0) mt_a += et > 0 ? fq : -fq;
+            } else {
+                pf_d += fq;
+                mn_d += en > 0 ? fq : -fq;
+                mt_d += et > 0 ? fq : -fq;
+                qn_d += q;
+                qt_d += en * et > 0 ? q : -q;
+            }
+        }
+    }
+    // g: points at dt_g
+    R ce_a = R(0), ce_d = R(0), cen_a = R(0), cen_d = R(0), Cface;
+    {
+        R un[9], ut[9], CC[9];
+        points_dt(Un, K.dtg, un);
+        points_dt(Ut, K.dtg, ut);
+        points_dt(recn(P + F_C * FS, x), K.dtg, CC);
+        Cface = CC[0];
+#pragma unroll
+        for (int a = 1; a < 9; ++a) {
+            const int en = e_n(a);
+            const R ce = CC[a] * e_dot(a, un[a], ut[a]);
+            if (a < 5) { ce_a += ce; if (en != 0) cen_a += en > 0 ? ce : -ce; }
+            else { ce_d += ce; cen_d += en > 0 ? ce : -ce; }
+        }
+    }
+    // h: points at dt_h (only e_n != 0 points carry C_p T q into the flux)
+    R th_a = R(0), th_d = R(0);
+    const RecN<R> T = recn(P + F_T * FS, x), cp = recn(P + F_CP * FS, x);
+    {
+        R un[9], ut[9], Tp[9], cpp[9];
+        points_dt(Un, K.dth, un);
+        points_dt(Ut, K.dth, ut);
+        points_dt(T, K.dth, Tp);
+        points_dt(cp, K.dth, cpp);
+#pragma unroll
+        for (int a = 1; a < 9; ++a) {
+            const int en = e_n(a);
+            if (en == 0) continue;
+            const R eu = e_dot(a, un[a], ut[a]);
+            const R q = eu + R(1.5) * eu * eu - R(0.5) * (un[a] * un[a] + ut[a] * ut[a]);
+            const R thq = (cpp[a] * Tp[a]) * q;
+            if (a < 5) th_a += en > 0 ? thq : -thq;
+            else th_d += en > 0 ? thq : -thq;
+        }
+    }
+    const RecN<R> p = recn(P + F_P * FS, x), mu = recn(P + F_MUC * FS, x);
+    const R lamf = face_value(P + F_LAM * FS, x);
+    const R muf = face_value(P + F_MU * FS, x);
+    const R af = R(0.5) - K.dtf, ag = R(0.5) - K.dtg, ah = R(0.5) - K.dth;
+    const R pl = p.l + af * p.gl, pr = p.r - af * p.gr;
+    const R ml = mu.l + ag * mu.gl, mr = mu.r - ag * mu.gr;
+    const R Tl = T.l + ah * T.gl, Tr = T.r - ah * T.gr;
+    const R pf = R(2.0 / 3.0) * p.o0 + R(1.0 / 6.0) * (pl + pr) + w0 * fq0 + w1 * pf_a + w5 * pf_d;
+    const R mn = R(1.0 / 6.0) * (pl - pr) + w1 * mn_a + w5 * mn_d;
+    const R mt = -(K.dtf * R(1.0 / 12.0)) * (p.dtl + p.dtr) + w1 * mt_a + w5 * mt_d;
+    const R Cf = Cface + K.Qg * (R(0.5) * (ml + mr) - mu.o0) + R(1.0 / 3.0) * ce_a + R(1.0 / 12.0) * ce_d;
+    const R Sg = R(0.5) * K.Qg * (ml - mr) + R(1.0 / 3.0) * cen_a + R(1.0 / 12.0) * cen_d;
+    const R Sh = R(1.0 / 6.0) * K.Cref * (Tl - Tr) + R(1.0 / 3.0) * th_a + R(1.0 / 12.0) * th_d;
+    const R Snn_p = R(1.0 / 6.0) * (pl + pr);
+    const R Snt_p = (K.dtf * R(1.0 / 36.0)) * (p.dtr - p.dtl);
+    const R Snn_q = w1 * qn_a + w5 * qn_d;
+    const R Snt_q = w5 * qt_d;
+    const R irf = wdiv(R(1), rho_f);
+    const R unf = R(3) * mn * irf, utf = R(3) * mt * irf;
+    const R th = K.th_coef * lamf * irf;
+    const R tf = K.tf_coef * muf * irf;
+    const R tg = K.tau_g - R(0.5);
+    const R cs2 = R(1.0 / 3.0);
+    FaceFlux<R> F;
+    F.Fh = (R(1) - th) * (cp.o0 * T.o0) * unf + th * Sh;
+    F.Fp = mn;
+    F.Fmn = (R(1) - tf) * cs2 * (pf + rho_f * unf * unf) + tf * (Snn_p + rho_f * Snn_q);
+    F.Fmt = (R(1) - tf) * cs2 * rho_f * unf * utf + tf * (Snt_p + rho_f * Snt_q);
+    F.Fc = (R(1) - tg) * Cf * unf + tg * Sg;
+    F.un = unf;
+    if (AXI) F.Fmn += -(K.dtf * R(1.0 / 9.0)) * rho_f * (normal_is_r ? unf0 : utf0) * inv_r;
+    return F;
+}
+
 // Step 3, x-faces of ring row r: lane l computes the face between columns
 // l+2 and l+3 (cells x0+l-1 and x0+l), at x = x0 + l.  In an axisymmetric
 // domain the stored fluxes are multiplied by the face area r_f = x0 + l.
-template <class R, bool AXI>
+template <class R, bool AXI, bool GEN>
 __device__ __forceinline__ void x_face(Smem<R>& S, int x0, int r, int row_in_chunk, int lane) {
     FaceIdx x;
     const int cL = lane + 2;
@@ -342,7 +501,9 @@ __device__ __forceinline__ void x_face(Smem<R>& S, int x0, int r, int row_in_chu
     x.Rm = x.Lm + 1;
     const int gf = x0 + lane;
     const R rf = AXI ? (R)gf : R(1);
-    FaceFlux<R> F = face_flux<R, AXI>(S.K, &S.P[0][0][0], x, F_U, F_V, true, (AXI && gf > 0) ? wdiv(R(1), rf) : R(0));
+    const R inv_rf = (AXI && gf > 0) ? wdiv(R(1), rf) : R(0);
+    FaceFlux<R> F = GEN ? face_flux_gen<R, AXI>(S.K, &S.P[0][0][0], x, F_U, F_V, true, inv_rf)
+                        : face_flux<R, AXI>(S.K, &S.P[0][0][0], x, F_U, F_V, true, inv_rf);
     if (AXI) {
         F.Fh *= rf; F.Fp *= rf; F.Fmn *= rf; F.Fmt *= rf; F.Fc *= rf; F.un *= rf;
     }
@@ -356,7 +517,7 @@ __device__ __forceinline__ void x_face(Smem<R>& S, int x0, int r, int row_in_chu
 
 // Step 3, y-faces of face row r (between rows r-1 and r), lane l < 31 at
 // column l+3 (cell x0 + l, radius x0 + l + 1/2 in an axisymmetric domain).
-template <class R, bool AXI>
+template <class R, bool AXI, bool GEN>
 __device__ __forceinline__ void y_face(Smem<R>& S, int x0, int r, int lane) {
     FaceIdx x;
     const int c = lane + kHalo;
@@ -369,7 +530,8 @@ __device__ __forceinline__ void y_face(Smem<R>& S, int x0, int r, int lane) {
     x.Rp = x.R + 1;
     x.Rm = x.R - 1;
     const R inv_r = AXI ? wdiv(R(1), (R)(x0 + lane) + R(0.5)) : R(0);
-    const FaceFlux<R> F = face_flux<R, AXI>(S.K, &S.P[0][0][0], x, F_V, F_U, false, inv_r);
+    const FaceFlux<R> F = GEN ? face_flux_gen<R, AXI>(S.K, &S.P[0][0][0], x, F_V, F_U, false, inv_r)
+                              : face_flux<R, AXI>(S.K, &S.P[0][0][0], x, F_V, F_U, false, inv_r);
     const int s = slot(r);
     S.YF[0][s][lane] = F.Fh;
     S.YF[1][s][lane] = F.Fp;
@@ -427,7 +589,7 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
     Rk[3] += cs2 * (-Fl * C * dmy + rho * K.gy - rho * v * D);         // row 4
     Rk[4] += C * K.kv * D;                                             // row 5 (R12)
     if (AXI)   // hoop stress Pi_thetatheta / r with the pressure advanced over dt_s (reading R24)
-        Rk[2] += cs2 * (P[F_P * FS + q] - R(0.5) * divF1 - R(2) * P[F_MU * FS + q] * u * irc) * irc;
+        Rk[2] += cs2 * (P[F_P * FS + q] - K.dtf * divF1 - R(2) * P[F_MU * FS + q] * u * irc) * irc;
 
     const R* in = reinterpret_cast<const R*>(K.st[stage]);
     const SV<R> ws = load_state(in, K.plane, c);
@@ -478,7 +640,7 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
 
 // One work item: the strip segment [x0, x0 + 31) x [y0, y1) of the domain
 // whose constants are in S.K (planar or axisymmetric, fixed per domain).
-template <class R, bool AXI>
+template <class R, bool AXI, bool GEN>
 __device__ __forceinline__ void sweep_item(Smem<R>& S, const StageLaunch& a, int x0, int y0, int y1) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const R* in = reinterpret_cast<const R*>(S.K.st[a.stage]);
@@ -488,7 +650,7 @@ __device__ __forceinline__ void sweep_item(Smem<R>& S, const StageLaunch& a, int
     __syncthreads();
     muc_rows<R, AXI>(S, x0, y0 - 2, 4);
     __syncthreads();
-    if (warp == 0 && lane < kStripX) y_face<R, AXI>(S, x0, y0, lane);
+    if (warp == 0 && lane < kStripX) y_face<R, AXI, GEN>(S, x0, y0, lane);
     // (the first chunk writes other ring rows: no barrier needed here)
 
     for (int j0 = y0; j0 < y1; j0 += kChunk) {
@@ -499,8 +661,8 @@ __device__ __forceinline__ void sweep_item(Smem<R>& S, const StageLaunch& a, int
         // one face at a time per thread (x then y) keeps register use low
 #pragma unroll 1
         for (int k = 0; k < 2; ++k) {
-            if (k == 0) x_face<R, AXI>(S, x0, j0 + warp, warp, lane);
-            else if (lane < kStripX) y_face<R, AXI>(S, x0, j0 + 1 + warp, lane);
+            if (k == 0) x_face<R, AXI, GEN>(S, x0, j0 + warp, warp, lane);
+            else if (lane < kStripX) y_face<R, AXI, GEN>(S, x0, j0 + 1 + warp, lane);
         }
         __syncthreads();
         const int r = j0 + warp;
@@ -536,8 +698,13 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) stage_kernel(Stage
         const int x0 = item.y * kStripX;
         const int y0 = item.z * a.seg;
         const int y1 = min(y0 + a.seg, S.K.ny);
-        if (S.K.axi) sweep_item<R, true>(S, a, x0, y0, y1);
-        else sweep_item<R, false>(S, a, x0, y0, y1);
+        if (S.K.gen) {   // some streaming step differs from 1/2 (reading R26)
+            if (S.K.axi) sweep_item<R, true, true>(S, a, x0, y0, y1);
+            else sweep_item<R, false, true>(S, a, x0, y0, y1);
+        } else {
+            if (S.K.axi) sweep_item<R, true, false>(S, a, x0, y0, y1);
+            else sweep_item<R, false, false>(S, a, x0, y0, y1);
+        }
     }
 }
 

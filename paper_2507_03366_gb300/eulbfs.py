@@ -52,7 +52,8 @@ class BC(ct.Structure):
 
 
 class Numerics(ct.Structure):
-    _fields_ = [("dt", ct.c_double), ("axisymmetric", ct.c_int)]
+    _fields_ = [("dt", ct.c_double), ("axisymmetric", ct.c_int), ("dt_stream_h", ct.c_double),
+                ("dt_stream_f", ct.c_double), ("dt_stream_g", ct.c_double)]
 
 
 _DP = ct.POINTER(ct.c_double)
@@ -153,6 +154,14 @@ def _bc(b) -> BC:
     return BC(sd(b.xlo), sd(b.xhi), sd(b.ylo), sd(b.yhi))
 
 
+def _numerics(case) -> Numerics:
+    """Time step, geometry and the three streaming steps (a case's
+    dt_stream stands for any step it leaves at 0)."""
+    base = float(getattr(case, "dt_stream", 0.5))
+    steps = [float(getattr(case, k, 0.0) or 0.0) or base for k in ("dt_h", "dt_f", "dt_g")]
+    return Numerics(case.dt, int(getattr(case, "axisymmetric", 0)), *steps)
+
+
 def domain_struct(case, keep: list) -> Domain:
     """Marshal a workloads.Case into an eulbfs_domain (arrays kept alive in `keep`)."""
     arrs = {k: np.ascontiguousarray(case.init[k], dtype=np.float64).ravel() for k in ("T", "Fl", "C", "u", "v", "p")}
@@ -160,7 +169,7 @@ def domain_struct(case, keep: list) -> Domain:
     init = Init(*[_ptr(arrs[k]) for k in ("T", "Fl", "C", "u", "v", "p")])
     if abs(case.dt_stream - 0.5) > 0:
         raise ValueError("libeulbfs uses the streaming step dt_s = 0.5 (lattice units)")
-    return Domain(Grid(case.nx, case.ny), _props(case.props), _bc(case.bc), Numerics(case.dt, int(getattr(case, "axisymmetric", 0))), init)
+    return Domain(Grid(case.nx, case.ny), _props(case.props), _bc(case.bc), _numerics(case), init)
 
 
 class Solver:

@@ -76,6 +76,12 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     d = eulbfs.domain_struct(case, keep)
     assert lib.eulbfs_batch_create(1, ct.byref(d), eulbfs.FP64, None, ct.byref(h)) == eulbfs.EINVAL
     assert b"axis" in lib.eulbfs_last_error()
+    # streaming steps lie in (0, 0.5]
+    case = wl.droplet(32)
+    case.dt_f = 0.6
+    d = eulbfs.domain_struct(case, keep)
+    assert lib.eulbfs_batch_create(1, ct.byref(d), eulbfs.FP64, None, ct.byref(h)) == eulbfs.EINVAL
+    assert b"streaming" in lib.eulbfs_last_error()
     # a hysteresis window needs theta_rec <= theta_adv
     case = wl.droplet(32)
     case.bc.ylo = wl.Side(wl.DIRICHLET_T, wl.NOSLIP, wl.WETTING_HYST, Tw=-0.5, theta_deg=90.0,
