@@ -5,6 +5,7 @@ weight, a coefficient, a dropped term, a boundary rule), builds it on the CPU
 and runs the pin that must fail on it.  This is what makes the pins evidence:
 a pin suite that passes on a broken oracle would prove nothing.
 """
+import concurrent.futures
 import os
 import subprocess
 import sys
@@ -41,8 +42,8 @@ MUTATIONS = [
      "test_three_phase_expansion_law"),
     ("gravity_sign", "FE[3] = CS2 * (Fsy + rho * s->P.gy + Fiy);", "FE[3] = CS2 * (Fsy - rho * s->P.gy + Fiy);",
      "test_hydrostatic_pressure"),
-    ("tau_h_heat_capacity", "const double tau_h = 0.5 + lamf / (rho_f * s->Cref * CS2 * dts);",
-     "const double tau_h = 0.5 + lamf / (rho_f * Cpf * CS2 * dts);", "test_pure_conduction_face_flux"),
+    ("tau_h_heat_capacity", "const double tau_h = 0.5 + lamf / (rho_f * s->Cref * CS2 * s->dth);",
+     "const double tau_h = 0.5 + lamf / (rho_f * Cpf * CS2 * s->dth);", "test_pure_conduction_face_flux"),
     ("reconstruction_offset_sign", "+ (y - (cj + 0.5)) * s->gry[f][q];", "- (y - (cj + 0.5)) * s->gry[f][q];",
      "test_linear_temperature_convective_diffusive_flux"),
     ("tie_rule_R7", "q[a][f] = 0.5 * (recon(s, f, Li, Lj, sx, sy) + recon(s, f, Ri, Rj, sx, sy));",
@@ -52,7 +53,7 @@ MUTATIONS = [
     ("heq_quadratic", "(Cref / Cp + eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));",
      "(Cref / Cp + eu / CS2 + eu * eu / (2.0 * CS2) - uu / (2.0 * CS2));", "test_equilibria_moments"),
     ("solid_branch_heat_capacity", "*T = H / cps;", "*T = H / cpl;", "test_enthalpy_inversion_values"),
-    ("wetting_sign_R11", "return vm + (2.0 * k - 1.0) * (4.0 * cos(th)", "return vm - (2.0 * k - 1.0) * (4.0 * cos(th)",
+    ("wetting_sign_R11", "return vm + (2.0 * k - 1.0) * (4.0 * cth", "return vm - (2.0 * k - 1.0) * (4.0 * cth",
      "test_contact_angle"),
     ("dirichlet_ghost", "2.0 * sd->Tw - vm : vm;", "sd->Tw : vm;", "test_neumann_two_phase_front"),
     ("noslip_tangential", "if (sd->flow == OR_BC_NOSLIP) return -vm;",
@@ -65,12 +66,12 @@ MUTATIONS = [
     ("axi_planar_divergence", "for (int k = 0; k < 5; ++k) divF[k] = (re * fe[k] - rw * fw[k]) / rc + (fn[k] - fs[k]);",
      "for (int k = 0; k < 5; ++k) divF[k] = (fe[k] - fw[k]) + (fn[k] - fs[k]);",
      AXI + "test_cylinder_conduction_mode_decay"),
-    ("axi_hoop_pressure_dropped", "FE[2] += CS2 * (s->prim[P_P][q] - s->N.dt_stream",
-     "FE[2] += CS2 * (0.0 * s->prim[P_P][q] - s->N.dt_stream",
+    ("axi_hoop_pressure_dropped", "FE[2] += CS2 * (s->prim[P_P][q] - s->dtf",
+     "FE[2] += CS2 * (0.0 * s->prim[P_P][q] - s->dtf",
      AXI + "test_uniform_pressure_is_force_free"),
-    ("axi_hoop_pressure_not_advanced", "s->prim[P_P][q] - s->N.dt_stream * divF[1] -", "s->prim[P_P][q] -",
+    ("axi_hoop_pressure_not_advanced", "s->prim[P_P][q] - s->dtf * divF[1] -", "s->prim[P_P][q] -",
      AXI + "test_uniform_radial_expansion"),
-    ("axi_hoop_pressure_not_advanced_stability", "s->prim[P_P][q] - s->N.dt_stream * divF[1] -", "s->prim[P_P][q] -",
+    ("axi_hoop_pressure_not_advanced_stability", "s->prim[P_P][q] - s->dtf * divF[1] -", "s->prim[P_P][q] -",
      AXI + "test_resting_drop_in_light_gas_stays_bounded"),
     ("axi_hoop_viscous_dropped", "2.0 * s->prim[P_MU][q] * u / rc) / rc;", "0.0 * s->prim[P_MU][q] * u / rc) / rc;",
      AXI + "test_stagnation_flow_residual_linear_part_vanishes"),
@@ -104,17 +105,37 @@ MUTATIONS = [
 ]
 
 
-@pytest.mark.parametrize("name,orig,planted,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_pin_catches_planted_mistake(name, orig, planted, pin, tmp_path):
+def _run_mutant(name, orig, planted, pin, workdir):
+    """Build the oracle with one planted mistake and run its pin; returns
+    (anchor found, pin exit code, pin output)."""
     src = open(SRC).read()
-    assert src.count(orig) == 1, f"mutation anchor for {name} not found exactly once"
-    mut_c = tmp_path / "mut.c"
-    mut_so = tmp_path / "libmut.so"
-    mut_c.write_text(src.replace(orig, planted))
+    if src.count(orig) != 1:
+        return False, None, ""
+    mut_c = os.path.join(workdir, name + ".c")
+    mut_so = os.path.join(workdir, "lib" + name + ".so")
+    with open(mut_c, "w") as f:
+        f.write(src.replace(orig, planted))
     subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-fPIC", "-shared", "-D_DEFAULT_SOURCE",
-                           "-I", os.path.join(ROOT, "oracle"), "-o", str(mut_so), str(mut_c), "-lm"])
-    env = dict(os.environ, EULBFS_ORACLE_LIB=str(mut_so))
+                           "-I", os.path.join(ROOT, "oracle"), "-o", mut_so, mut_c, "-lm"])
+    env = dict(os.environ, EULBFS_ORACLE_LIB=mut_so)
     node = pin if "::" in pin else PINS + pin
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", node],
                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, f"pin {pin} passed on an oracle with '{name}' planted:\n{r.stdout[-2000:]}"
+    return True, r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def mutant_results(tmp_path_factory):
+    """All mutants built and their pins run concurrently (each in its own
+    process), so the suite costs about one pin run per core."""
+    workdir = str(tmp_path_factory.mktemp("mutants"))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        futs = {m[0]: ex.submit(_run_mutant, *m, workdir) for m in MUTATIONS}
+        return {k: f.result() for k, f in futs.items()}
+
+
+@pytest.mark.parametrize("name,orig,planted,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pin_catches_planted_mistake(name, orig, planted, pin, mutant_results):
+    found, code, out = mutant_results[name]
+    assert found, f"mutation anchor for {name} not found exactly once"
+    assert code != 0, f"pin {pin} passed on an oracle with '{name}' planted:\n{out}"
