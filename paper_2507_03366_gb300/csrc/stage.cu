@@ -35,14 +35,35 @@ namespace {
 constexpr int RW = kStripX + 2 * kHalo;   // ring columns: strip plus halo (37)
 constexpr int RING = 16;                  // ring rows (power of two)
 constexpr int NT = kStageThreads;         // 8 warps
-enum { F_T, F_FL, F_CP, F_RHO, F_LAM, F_MU, F_P, F_U, F_V, F_C, F_MUC, NF };
-constexpr int FS = RING * RW;             // field stride in the ring
+
+// Two fields of a cell side by side, read and written with one 8-byte
+// (FP64: 16-byte) shared-memory access.
+template <class R> struct Pair;
+template <> struct Pair<float> { using T = float2; };
+template <> struct Pair<double> { using T = double2; };
+template <class R> using P2 = typename Pair<R>::T;
+
+// Derived fields of the ring rows (row r in slot r & 15), paired by the
+// places that read them together: every face point needs (u, v), (rho, C)
+// and (T, C_p); p is needed at every point and mu_c at the cell and outer
+// n-neighbours; lambda and mu only at the face.
+template <class R>
+struct Ring {
+    P2<R> uv[RING][RW];       // u, v
+    P2<R> rc[RING][RW];       // rho, C
+    P2<R> tc[RING][RW];       // T, C_p
+    P2<R> pm[RING][RW];       // p, mu_c
+    P2<R> lm[RING][RW];       // lambda, mu
+    R fl[RING][RW];           // F_l
+};
 
 template <class R>
 struct Smem {
-    R P[NF][RING][RW];        // derived fields, ring of rows (row r in slot r & 15)
-    R YF[6][RING][32];        // y-face fluxes, ring of face rows
-    R XF[6][kChunk][32];      // x-face fluxes of the current chunk
+    Ring<R> P;
+    // face fluxes in pairs (F_h, F_p), (F_mx, F_my), (F_C, u_n): y-faces in a
+    // ring of face rows, x-faces of the current chunk
+    P2<R> YF[3][RING][32];
+    P2<R> XF[3][kChunk][32];
     Consts<R> K;
 };
 
@@ -51,16 +72,12 @@ __device__ __forceinline__ int slot(int r) { return r & (RING - 1); }
 // Step 1: rows [r0, r0 + nrows) of the strip (all RW columns).
 template <class R>
 __device__ __forceinline__ void store_prim(Smem<R>& S, int s, int cc, const Prim<R>& q) {
-    S.P[F_T][s][cc] = q.T;
-    S.P[F_FL][s][cc] = q.Fl;
-    S.P[F_CP][s][cc] = q.cp;
-    S.P[F_RHO][s][cc] = q.rho;
-    S.P[F_LAM][s][cc] = q.lam;
-    S.P[F_MU][s][cc] = q.mu;
-    S.P[F_P][s][cc] = q.p;
-    S.P[F_U][s][cc] = q.u;
-    S.P[F_V][s][cc] = q.v;
-    S.P[F_C][s][cc] = q.C;
+    S.P.uv[s][cc] = P2<R>{q.u, q.v};
+    S.P.rc[s][cc] = P2<R>{q.rho, q.C};
+    S.P.tc[s][cc] = P2<R>{q.T, q.cp};
+    S.P.pm[s][cc].x = q.p;     // mu_c follows in step 2
+    S.P.lm[s][cc] = P2<R>{q.lam, q.mu};
+    S.P.fl[s][cc] = q.Fl;
 }
 
 template <class R>
@@ -98,14 +115,14 @@ __device__ __forceinline__ void load_rows(Smem<R>& S, const R* in, int x0, int r
 // is the 5-point one, or in an axisymmetric domain the conservative
 // (1/r) d/dr (r dC/dr) + d2C/dz2 with faces at r = gx and gx + 1.
 template <class R, bool AXI>
-__device__ __forceinline__ R chem_potential(const Consts<R>& K, const R* C, int s0, int sN, int sS, int gx) {
-    const R c = C[s0];
+__device__ __forceinline__ R chem_potential(const Consts<R>& K, const P2<R>* RC, int s0, int sN, int sS, int gx) {
+    const R c = RC[s0].y, ce = RC[s0 + 1].y, cw = RC[s0 - 1].y, cn = RC[sN].y, cs = RC[sS].y;
     R lap;
     if (AXI) {
         const R rw = (R)gx, re = rw + R(1);
-        lap = wdiv(re * (C[s0 + 1] - c) - rw * (c - C[s0 - 1]), rw + R(0.5)) + (C[sN] + C[sS] - R(2) * c);
+        lap = wdiv(re * (ce - c) - rw * (c - cw), rw + R(0.5)) + (cn + cs - R(2) * c);
     } else {
-        lap = C[s0 + 1] + C[s0 - 1] + C[sN] + C[sS] - R(4) * c;
+        lap = ce + cw + cn + cs - R(4) * c;
     }
     return R(2) * K.beta * c * (c - R(1)) * (R(2) * c - R(1)) - K.kappa * lap;
 }
@@ -119,14 +136,14 @@ __device__ __forceinline__ void muc_rows(Smem<R>& S, int x0, int r0, int nrows) 
     const Consts<R>& K = S.K;
     constexpr int NC = RW - 2;
     const int total = nrows * NC;
-    const R* C = &S.P[F_C][0][0];
+    const P2<R>* C = &S.P.rc[0][0];
     if (x0 >= kHalo - 1 && x0 + NC - (kHalo - 1) <= K.nx && r0 >= 0 && r0 + nrows <= K.ny) {
         // no wall ghost among these cells: the Laplacian in place
         for (int idx = threadIdx.x; idx < total; idx += NT) {
             const int rr = idx / NC, cc = 1 + idx - rr * NC;
             const int gy = r0 + rr;
             const int s0 = slot(gy) * RW + cc;
-            S.P[F_MUC][slot(gy)][cc] =
+            S.P.pm[slot(gy)][cc].y =
                 chem_potential<R, AXI>(K, C, s0, slot(gy + 1) * RW + cc, slot(gy - 1) * RW + cc, x0 + cc - kHalo);
         }
         return;
@@ -147,7 +164,7 @@ __device__ __forceinline__ void muc_rows(Smem<R>& S, int x0, int r0, int nrows) 
         if (!deep)
             mu = chem_potential<R, AXI>(K, C, slot(my) * RW + mc, slot(my + 1) * RW + mc, slot(my - 1) * RW + mc,
                                 x0 + mc - kHalo);
-        S.P[F_MUC][slot(gy)][cc] = mu;
+        S.P.pm[slot(gy)][cc].y = mu;
     }
 }
 
@@ -166,16 +183,25 @@ template <class R>
 struct Rec { R l, r, o0, dtl, dtr; };
 
 template <class R>
-__device__ __forceinline__ Rec<R> rec(const R* f, const FaceIdx& x) {
+__device__ __forceinline__ Rec<R> rec_of(R l, R r, R ll, R rr, R lp, R lm, R rp, R rm) {
     Rec<R> z;
-    z.l = f[x.L];
-    z.r = f[x.R];
-    const R lf = z.l + R(0.25) * (z.r - f[x.LL]);
-    const R rf = z.r - R(0.25) * (f[x.RR] - z.l);
+    z.l = l;
+    z.r = r;
+    const R lf = l + R(0.25) * (r - ll);
+    const R rf = r - R(0.25) * (rr - l);
     z.o0 = R(0.5) * (lf + rf);
-    z.dtl = f[x.Lp] - f[x.Lm];
-    z.dtr = f[x.Rp] - f[x.Rm];
+    z.dtl = lp - lm;
+    z.dtr = rp - rm;
     return z;
+}
+
+// The reconstruction pieces of both fields of a pair.
+template <class R>
+__device__ __forceinline__ void rec2(const P2<R>* f, const FaceIdx& x, Rec<R>& a, Rec<R>& b) {
+    const P2<R> l = f[x.L], r = f[x.R], ll = f[x.LL], rr = f[x.RR];
+    const P2<R> lp = f[x.Lp], lm = f[x.Lm], rp = f[x.Rp], rm = f[x.Rm];
+    a = rec_of(l.x, r.x, ll.x, rr.x, lp.x, lm.x, rp.x, rm.x);
+    b = rec_of(l.y, r.y, ll.y, rr.y, lp.y, lm.y, rp.y, rm.y);
 }
 
 // Values at the 9 points in the order 0..8 of the face frame:
@@ -196,11 +222,18 @@ __device__ __forceinline__ void all_points(const Rec<R>& z, R o[9]) {
 }
 
 template <class R>
-__device__ __forceinline__ R face_value(const R* f, const FaceIdx& x) {
-    const R l = f[x.L], r = f[x.R];
-    const R lf = l + R(0.25) * (r - f[x.LL]);
-    const R rf = r - R(0.25) * (f[x.RR] - l);
+__device__ __forceinline__ R face_value(R l, R r, R ll, R rr) {
+    const R lf = l + R(0.25) * (r - ll);
+    const R rf = r - R(0.25) * (rr - l);
     return R(0.5) * (lf + rf);
+}
+
+// Face values of both fields of a pair (cells L, R and their outer n-neighbours).
+template <class R>
+__device__ __forceinline__ void face_value2(const P2<R>* f, const FaceIdx& x, R& a, R& b) {
+    const P2<R> l = f[x.L], r = f[x.R], ll = f[x.LL], rr = f[x.RR];
+    a = face_value(l.x, r.x, ll.x, rr.x);
+    b = face_value(l.y, r.y, ll.y, rr.y);
 }
 
 // Sec. 2.5 steps (2)-(4) and Eq. 53 for one face.
@@ -225,20 +258,24 @@ __device__ __forceinline__ R face_value(const R* f, const FaceIdx& x) {
 // cs^2 dt_s (-rho_f cs^2 u_r / r) = -rho_f u_r / (18 r) with the face values;
 // inv_r = 1 / r of the face (0 on the axis, where the face area is zero).
 template <class R, bool AXI>
-__device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const R* P, const FaceIdx& x, int fUn, int fUt,
+__device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const Ring<R>& P, const FaceIdx& x, bool normal_x,
                                                  bool normal_is_r, R inv_r) {
     R un[9], ut[9], rr[9], CC[9];
-    all_points(rec(P + fUn * FS, x), un);
-    all_points(rec(P + fUt * FS, x), ut);
-    all_points(rec(P + F_RHO * FS, x), rr);
-    all_points(rec(P + F_C * FS, x), CC);
-    const Rec<R> T = rec(P + F_T * FS, x);
-    const Rec<R> cp = rec(P + F_CP * FS, x);
-    const Rec<R> p = rec(P + F_P * FS, x);
-    const R mu_l = P[F_MUC * FS + x.L], mu_r = P[F_MUC * FS + x.R];
-    const R mu_0 = face_value(P + F_MUC * FS, x);
-    const R lamf = face_value(P + F_LAM * FS, x);
-    const R muf = face_value(P + F_MU * FS, x);
+    {
+        Rec<R> ru, rv, rrho, rC;
+        rec2(&P.uv[0][0], x, ru, rv);
+        all_points(normal_x ? ru : rv, un);
+        all_points(normal_x ? rv : ru, ut);
+        rec2(&P.rc[0][0], x, rrho, rC);
+        all_points(rrho, rr);
+        all_points(rC, CC);
+    }
+    Rec<R> T, cp, p, muc;
+    rec2(&P.tc[0][0], x, T, cp);
+    rec2(&P.pm[0][0], x, p, muc);
+    const R mu_l = muc.l, mu_r = muc.r, mu_0 = muc.o0;
+    R lamf, muf;
+    face_value2(&P.lm[0][0], x, lamf, muf);
 
     // side-point temperatures and heat capacities (e_n != 0 points only)
     const R Ts[9] = {T.o0, T.l, R(0), T.r, R(0), T.l - R(0.25) * T.dtl, T.r - R(0.25) * T.dtr,
@@ -340,16 +377,24 @@ template <class R>
 struct RecN { R l, r, gl, gr, o0, dtl, dtr; };
 
 template <class R>
-__device__ __forceinline__ RecN<R> recn(const R* f, const FaceIdx& x) {
+__device__ __forceinline__ RecN<R> recn_of(R l, R r, R ll, R rr, R lp, R lm, R rp, R rm) {
     RecN<R> z;
-    z.l = f[x.L];
-    z.r = f[x.R];
-    z.gl = R(0.5) * (z.r - f[x.LL]);
-    z.gr = R(0.5) * (f[x.RR] - z.l);
+    z.l = l;
+    z.r = r;
+    z.gl = R(0.5) * (r - ll);
+    z.gr = R(0.5) * (rr - l);
     z.o0 = R(0.5) * ((z.l + R(0.5) * z.gl) + (z.r - R(0.5) * z.gr));
-    z.dtl = f[x.Lp] - f[x.Lm];
-    z.dtr = f[x.Rp] - f[x.Rm];
+    z.dtl = lp - lm;
+    z.dtr = rp - rm;
     return z;
+}
+
+template <class R>
+__device__ __forceinline__ void recn2(const P2<R>* f, const FaceIdx& x, RecN<R>& a, RecN<R>& b) {
+    const P2<R> l = f[x.L], r = f[x.R], ll = f[x.LL], rr = f[x.RR];
+    const P2<R> lp = f[x.Lp], lm = f[x.Lm], rp = f[x.Rp], rm = f[x.Rm];
+    a = recn_of(l.x, r.x, ll.x, rr.x, lp.x, lm.x, rp.x, rm.x);
+    b = recn_of(l.y, r.y, ll.y, rr.y, lp.y, lm.y, rp.y, rm.y);
 }
 
 // Values at the 9 points x_f - e_a dt (order as in all_points); a = 1/2 - dt.
@@ -379,18 +424,22 @@ __device__ __forceinline__ R e_dot(int a, R un, R ut) {
 }
 
 template <class R, bool AXI>
-__device__ __forceinline__ FaceFlux<R> face_flux_gen(const Consts<R>& K, const R* P, const FaceIdx& x, int fUn, int fUt,
-                                                  bool normal_is_r, R inv_r) {
+__device__ __forceinline__ FaceFlux<R> face_flux_gen(const Consts<R>& K, const Ring<R>& P, const FaceIdx& x,
+                                                     bool normal_x, bool normal_is_r, R inv_r) {
     const R w0 = R(4.0 / 9.0), w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
-    const RecN<R> Un = recn(P + fUn * FS, x), Ut = recn(P + fUt * FS, x);
+    RecN<R> Un, Ut;
+    recn2(&P.uv[0][0], x, Un, Ut);
+    if (!normal_x) { const RecN<R> t = Un; Un = Ut; Ut = t; }
     // f: points at dt_f
     R fq0, pf_a = R(0), mn_a = R(0), mt_a = R(0), pf_d = R(0), mn_d = R(0), mt_d = R(0);
     R qn_a = R(0), qn_d = R(0), qt_d = R(0), rho_f, unf0, utf0;
+    RecN<R> Rho, Cc;
+    recn2(&P.rc[0][0], x, Rho, Cc);
     {
         R un[9], ut[9], rr[9];
         points_dt(Un, K.dtf, un);
         points_dt(Ut, K.dtf, ut);
-        points_dt(recn(P + F_RHO * FS, x), K.dtf, rr);
+        points_dt(Rho, K.dtf, rr);
         rho_f = rr[0];
         unf0 = un[0];
         utf0 = ut[0];
@@ -420,7 +469,7 @@ __device__ __forceinline__ FaceFlux<R> face_flux_gen(const Consts<R>& K, const R
         R un[9], ut[9], CC[9];
         points_dt(Un, K.dtg, un);
         points_dt(Ut, K.dtg, ut);
-        points_dt(recn(P + F_C * FS, x), K.dtg, CC);
+        points_dt(Cc, K.dtg, CC);
         Cface = CC[0];
 #pragma unroll
         for (int a = 1; a < 9; ++a) {
@@ -432,7 +481,8 @@ __device__ __forceinline__ FaceFlux<R> face_flux_gen(const Consts<R>& K, const R
     }
     // h: points at dt_h (only e_n != 0 points carry C_p T q into the flux)
     R th_a = R(0), th_d = R(0);
-    const RecN<R> T = recn(P + F_T * FS, x), cp = recn(P + F_CP * FS, x);
+    RecN<R> T, cp;
+    recn2(&P.tc[0][0], x, T, cp);
     {
         R un[9], ut[9], Tp[9], cpp[9];
         points_dt(Un, K.dth, un);
@@ -450,9 +500,10 @@ __device__ __forceinline__ FaceFlux<R> face_flux_gen(const Consts<R>& K, const R
             else th_d += en > 0 ? thq : -thq;
         }
     }
-    const RecN<R> p = recn(P + F_P * FS, x), mu = recn(P + F_MUC * FS, x);
-    const R lamf = face_value(P + F_LAM * FS, x);
-    const R muf = face_value(P + F_MU * FS, x);
+    RecN<R> p, mu;
+    recn2(&P.pm[0][0], x, p, mu);
+    R lamf, muf;
+    face_value2(&P.lm[0][0], x, lamf, muf);
     const R af = R(0.5) - K.dtf, ag = R(0.5) - K.dtg, ah = R(0.5) - K.dth;
     const R pl = p.l + af * p.gl, pr = p.r - af * p.gr;
     const R ml = mu.l + ag * mu.gl, mr = mu.r - ag * mu.gr;
@@ -502,17 +553,14 @@ __device__ __forceinline__ void x_face(Smem<R>& S, int x0, int r, int row_in_chu
     const int gf = x0 + lane;
     const R rf = AXI ? (R)gf : R(1);
     const R inv_rf = (AXI && gf > 0) ? wdiv(R(1), rf) : R(0);
-    FaceFlux<R> F = GEN ? face_flux_gen<R, AXI>(S.K, &S.P[0][0][0], x, F_U, F_V, true, inv_rf)
-                        : face_flux<R, AXI>(S.K, &S.P[0][0][0], x, F_U, F_V, true, inv_rf);
+    FaceFlux<R> F = GEN ? face_flux_gen<R, AXI>(S.K, S.P, x, true, true, inv_rf)
+                        : face_flux<R, AXI>(S.K, S.P, x, true, true, inv_rf);
     if (AXI) {
         F.Fh *= rf; F.Fp *= rf; F.Fmn *= rf; F.Fmt *= rf; F.Fc *= rf; F.un *= rf;
     }
-    S.XF[0][row_in_chunk][lane] = F.Fh;
-    S.XF[1][row_in_chunk][lane] = F.Fp;
-    S.XF[2][row_in_chunk][lane] = F.Fmn;   // x-momentum
-    S.XF[3][row_in_chunk][lane] = F.Fmt;   // y-momentum
-    S.XF[4][row_in_chunk][lane] = F.Fc;
-    S.XF[5][row_in_chunk][lane] = F.un;
+    S.XF[0][row_in_chunk][lane] = P2<R>{F.Fh, F.Fp};
+    S.XF[1][row_in_chunk][lane] = P2<R>{F.Fmn, F.Fmt};   // x-, y-momentum
+    S.XF[2][row_in_chunk][lane] = P2<R>{F.Fc, F.un};
 }
 
 // Step 3, y-faces of face row r (between rows r-1 and r), lane l < 31 at
@@ -530,15 +578,12 @@ __device__ __forceinline__ void y_face(Smem<R>& S, int x0, int r, int lane) {
     x.Rp = x.R + 1;
     x.Rm = x.R - 1;
     const R inv_r = AXI ? wdiv(R(1), (R)(x0 + lane) + R(0.5)) : R(0);
-    const FaceFlux<R> F = GEN ? face_flux_gen<R, AXI>(S.K, &S.P[0][0][0], x, F_V, F_U, false, inv_r)
-                              : face_flux<R, AXI>(S.K, &S.P[0][0][0], x, F_V, F_U, false, inv_r);
+    const FaceFlux<R> F = GEN ? face_flux_gen<R, AXI>(S.K, S.P, x, false, false, inv_r)
+                              : face_flux<R, AXI>(S.K, S.P, x, false, false, inv_r);
     const int s = slot(r);
-    S.YF[0][s][lane] = F.Fh;
-    S.YF[1][s][lane] = F.Fp;
-    S.YF[2][s][lane] = F.Fmt;   // x-momentum
-    S.YF[3][s][lane] = F.Fmn;   // y-momentum
-    S.YF[4][s][lane] = F.Fc;
-    S.YF[5][s][lane] = F.un;
+    S.YF[0][s][lane] = P2<R>{F.Fh, F.Fp};
+    S.YF[1][s][lane] = P2<R>{F.Fmt, F.Fmn};   // x-, y-momentum
+    S.YF[2][s][lane] = P2<R>{F.Fc, F.un};
 }
 
 // Step 4 for the cell (r, x0 + lane).
@@ -554,23 +599,30 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
     // Eq. 52; axisymmetric: the x-face fluxes carry their areas r_f, divided
     // here by the cell volume r_i = gx + 1/2 (per radian)
     const R irc = AXI ? wdiv(R(1), (R)gx + R(0.5)) : R(1);
-    R Rk[5];
+    R Rk[5], divu;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const R dx = S.XF[k][row_in_chunk][lane + 1] - S.XF[k][row_in_chunk][lane];
-        Rk[k] = -((AXI ? dx * irc : dx) + (S.YF[k][sn][lane] - S.YF[k][sr][lane]));
+    for (int k = 0; k < 3; ++k) {
+        const P2<R> e = S.XF[k][row_in_chunk][lane + 1], w = S.XF[k][row_in_chunk][lane];
+        const P2<R> n = S.YF[k][sn][lane], so = S.YF[k][sr][lane];
+        const R dx0 = e.x - w.x, dx1 = e.y - w.y;
+        const R d0 = -((AXI ? dx0 * irc : dx0) + (n.x - so.x));
+        const R d1 = (AXI ? dx1 * irc : dx1) + (n.y - so.y);
+        Rk[2 * k] = d0;
+        if (k < 2) Rk[2 * k + 1] = -d1;
+        else divu = d1;
     }
-    const R dxu = S.XF[5][row_in_chunk][lane + 1] - S.XF[5][row_in_chunk][lane];
-    const R divu = (AXI ? dxu * irc : dxu) + (S.YF[5][sn][lane] - S.YF[5][sr][lane]);
     const R divF1 = -Rk[1];   // div(rho cs^2 u), the pressure-flux divergence
 
-    const R* P = &S.P[0][0][0];
-    const R T = P[F_T * FS + q], Fl = P[F_FL * FS + q], Cp = P[F_CP * FS + q];
-    const R rho = P[F_RHO * FS + q], u = P[F_U * FS + q], v = P[F_V * FS + q], C = P[F_C * FS + q];
-    const R drx = R(0.5) * (P[F_RHO * FS + q + 1] - P[F_RHO * FS + q - 1]);
-    const R dry = R(0.5) * (P[F_RHO * FS + qn] - P[F_RHO * FS + qs]);
-    const R dmx = R(0.5) * (P[F_MUC * FS + q + 1] - P[F_MUC * FS + q - 1]);
-    const R dmy = R(0.5) * (P[F_MUC * FS + qn] - P[F_MUC * FS + qs]);
+    const Ring<R>& P = S.P;
+    const P2<R> tc = (&P.tc[0][0])[q], rc = (&P.rc[0][0])[q], uv = (&P.uv[0][0])[q];
+    const R T = tc.x, Cp = tc.y, rho = rc.x, C = rc.y, u = uv.x, v = uv.y;
+    const R Fl = (&P.fl[0][0])[q];
+    const P2<R>* RC = &P.rc[0][0];
+    const P2<R>* PM = &P.pm[0][0];
+    const R drx = R(0.5) * (RC[q + 1].x - RC[q - 1].x);
+    const R dry = R(0.5) * (RC[qn].x - RC[qs].x);
+    const R dmx = R(0.5) * (PM[q + 1].y - PM[q - 1].y);
+    const R dmy = R(0.5) * (PM[qn].y - PM[qs].y);
     R dfs;
     if (stage == 0) {   // reading R14: lagged dF_s/dt, fixed over the step
         R* Fsp = reinterpret_cast<R*>(K.Fsp);
@@ -589,7 +641,7 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
     Rk[3] += cs2 * (-Fl * C * dmy + rho * K.gy - rho * v * D);         // row 4
     Rk[4] += C * K.kv * D;                                             // row 5 (R12)
     if (AXI)   // hoop stress Pi_thetatheta / r with the pressure advanced over dt_s (reading R24)
-        Rk[2] += cs2 * (P[F_P * FS + q] - K.dtf * divF1 - R(2) * P[F_MU * FS + q] * u * irc) * irc;
+        Rk[2] += cs2 * (PM[q].x - K.dtf * divF1 - R(2) * (&P.lm[0][0])[q].y * u * irc) * irc;
 
     const R* in = reinterpret_cast<const R*>(K.st[stage]);
     const SV<R> ws = load_state(in, K.plane, c);
