@@ -643,9 +643,9 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
     if (AXI)   // hoop stress Pi_thetatheta / r with the pressure advanced over dt_s (reading R24)
         Rk[2] += cs2 * (PM[q].x - K.dtf * divF1 - R(2) * (&P.lm[0][0])[q].y * u * irc) * irc;
 
-    const R* in = reinterpret_cast<const R*>(K.st[stage]);
-    const SV<R> ws = load_state(in, K.plane, c);
+    // stage 0 reads W^n as its input: one load serves both
     const SV<R> wn = load_state(reinterpret_cast<const R*>(K.st[0]), K.plane, c);
+    const SV<R> ws = stage == 0 ? wn : load_state(reinterpret_cast<const R*>(K.st[stage]), K.plane, c);
     SV<R> o;
     if constexpr (sizeof(R) == 8) {
         // Eq. 58 as written

@@ -29,10 +29,16 @@ def _built():
 def assert_fields_close(g, r, rtol, keys=FIELDS, what="", floor=1e-12):
     """Max-norm error of each field relative to the field's magnitude (at
     least `floor`); the two velocity components share the speed scale (one is
-    pure round-off noise in the quasi-1D problems)."""
+    pure round-off noise in the quasi-1D problems).  T is recovered from the
+    enthalpy (Eq. 5-6: T = (H - L F_l) / C_p, C_p = O(1) here), so its
+    round-off is relative to |H| as well as to |T|: a droplet near T_m = 0
+    has |T| << |H|."""
     speed = max(float(np.max(np.abs(r["u"]))), float(np.max(np.abs(r["v"]))), floor)
+    hscale = float(np.max(np.abs(r["H"]))) if "H" in r else 0.0
     for k in keys:
         scale = speed if k in ("u", "v") else max(float(np.max(np.abs(r[k]))), floor)
+        if k == "T":
+            scale = max(scale, hscale)
         err = float(np.max(np.abs(g[k] - r[k])))
         assert err <= rtol * scale, f"{what} field {k}: max|gpu - oracle| = {err:.3e} > {rtol:g} * {scale:.3e}"
 
