@@ -37,11 +37,11 @@ STAGES = 3
 # operations (FFMA counted as 2) and warp instructions issued.  They are the
 # formulation's arithmetic and the kernel's instruction stream, so they change
 # only with the face/cell algebra or the code.
-FP32_FLOPS_PER_CELL_STAGE = {"rz": 1144, "xy": 1100}
-WARP_INST_PER_CELL_STAGE = {"rz": 52.8, "xy": 50.2}
+FP32_FLOPS_PER_CELL_STAGE = {"rz": 1142, "xy": 1100}
+WARP_INST_PER_CELL_STAGE = {"rz": 48.6, "xy": 46.3}
 # DRAM bytes per cell per launch of the stage kernel (ncu, average of the 3
 # stages of the same capture, scaled by cells).
-DRAM_BYTES_PER_CELL_LAUNCH = 64.5
+DRAM_BYTES_PER_CELL_LAUNCH = 64.9
 # Peaks from unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x SM clock;
 # 4 warp instructions issued per SM per clock (one per scheduler).
 SMS, FP32_LANES_PER_SM, ISSUE_PER_SM_CLK = 152, 128, 4
