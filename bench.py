@@ -42,9 +42,13 @@ WARP_INST_PER_CELL_STAGE = {"rz": 48.6, "xy": 46.3}
 # DRAM bytes per cell per launch of the stage kernel (ncu, average of the 3
 # stages of the same capture, scaled by cells).
 DRAM_BYTES_PER_CELL_LAUNCH = 64.9
+# FP64 operations per cell per stage of the FP64 stage kernel (DFMA counted as
+# 2), from the ncu counters of one capture of each geometry.
+FP64_FLOPS_PER_CELL_STAGE = {"rz": 1216, "xy": 1143}
 # Peaks from unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x SM clock;
-# 4 warp instructions issued per SM per clock (one per scheduler).
-SMS, FP32_LANES_PER_SM, ISSUE_PER_SM_CLK = 152, 128, 4
+# 4 warp instructions issued per SM per clock (one per scheduler); 2 FP64
+# FMA lanes per SM (ncu's sustained DFMA peak) x 2 flops x SM clock.
+SMS, FP32_LANES_PER_SM, ISSUE_PER_SM_CLK, FP64_LANES_PER_SM = 152, 128, 4, 2
 
 
 def parse():
@@ -309,6 +313,14 @@ def main():
         ms64 = e0.elapsed_time(e1)
         fp64 = {"value": cells * args.fp64_steps / (ms64 * 1e-3) / 1e9, "unit": "GCUPS",
                 "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps}
+        f64 = FP64_FLOPS_PER_CELL_STAGE[args.geometry]
+        if f64:
+            # the FP64 step is bound by the FP64 pipe (85 % busy in ncu)
+            fp64_peak = SMS * FP64_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
+            ach64 = f64 * cells * STAGES * args.fp64_steps / (ms64 * 1e-3) / 1e12
+            fp64["roofline"] = {"bound": "alu", "achieved": ach64, "peak": fp64_peak, "unit": "TFLOP/s",
+                                "frac": ach64 / fp64_peak, "kernel": "eulbfs::stage_kernel<double>",
+                                "peak_source": "unit counts x max SM clock (152 x 2 x 2 x %.0f MHz)" % clk_mhz}
         s64.close()
 
     # ---- end to end through the public API with host buffers -------------------
