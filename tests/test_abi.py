@@ -76,6 +76,10 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     d = eulbfs.domain_struct(case, keep)
     assert lib.eulbfs_batch_create(1, ct.byref(d), eulbfs.FP64, None, ct.byref(h)) == eulbfs.EINVAL
     assert b"axis" in lib.eulbfs_last_error()
+    # a domain of more than 2^31 cells is refused before any array is read
+    big = eulbfs.Domain(eulbfs.Grid(65536, 32769), d.props, d.bc, d.num, eulbfs.Init())
+    assert lib.eulbfs_batch_create(1, ct.byref(big), eulbfs.FP32C, None, ct.byref(h)) == eulbfs.EINVAL
+    assert b"too large" in lib.eulbfs_last_error()
     # streaming steps lie in (0, 0.5]
     case = wl.droplet(32)
     case.dt_f = 0.6
