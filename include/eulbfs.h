@@ -8,10 +8,11 @@
  * local D2Q9 equilibria (Eq. 54-56, 13/16, 35/37, 44/46, 53), cell sources
  * (Eq. 51), SSP-RK3 (Eq. 58) and enthalpy inversion (Eq. 5-7).
  *
- * Units are lattice units: cell size 1, lattice speed 1, cs^2 = 1/3 and the
- * streaming step dt_s = 0.5, so the surrounding points x_f - e_a dt_s of a
- * face lie on the neighbouring cell centres and face midpoints (Sec. 2.5
- * step (1): they must stay inside the two cells of the face).
+ * Units are lattice units: cell size 1, lattice speed 1, cs^2 = 1/3 and by
+ * default the streaming step dt_s = 0.5, so the surrounding points
+ * x_f - e_a dt_s of a face lie on the neighbouring cell centres and face
+ * midpoints (Sec. 2.5 step (1): they must stay inside the two cells of the
+ * face).  Each distribution's step can be set in eulbfs_numerics.
  * Arrays are row-major with x fastest: element (i, j) is at j*nx + i.
  *
  * Conventions for every call:
