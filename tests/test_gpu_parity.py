@@ -309,3 +309,51 @@ def test_nonfinite_state_is_reported(precision):
     with pytest.raises(eulbfs.EulbfsError) as e:
         s.diag()
     assert e.value.code == eulbfs.ENONFINITE
+
+
+# ---------------------------------------------------------------------------
+# Long runs of the two Stefan problems at their full sizes, both precisions,
+# against the closed forms (Neumann front, Eq. 59-60 one-phase limit; the
+# mass-conservation displacement (1 - rho_s/rho_l) x_s of Sec. 3.2).
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [eulbfs.FP64, eulbfs.FP32C])
+def test_conductive_20k_steps_front_follows_neumann(precision):
+    """Conductive freezing, 256 x 4, 20 000 steps: the front stays within 1 %
+    of 2 k sqrt(alpha t) once it is 16 cells from the wall."""
+    c = wl.conductive(256, 4)
+    k = wl.neumann_k(0.1)
+    s = eulbfs.Solver([c], precision=precision)
+    fronts = []
+    for _ in range(4):
+        s.step(5000)
+        d = s.diag()
+        xs = 2 * k * math.sqrt(0.1 * d["t"])
+        if xs >= 16.0:
+            assert abs(d["front_pos"] / xs - 1.0) < 0.01, (d["t"], d["front_pos"], xs)
+        fronts.append(d["front_pos"])
+    assert d["step"] == 20000 and fronts[-1] > 16.0
+
+
+def test_three_phase_long_run_fp32c_against_fp64():
+    """Three-phase Stefan, 1024 x 4, St = 1, 20 000 steps: the FP64 step follows
+    the Neumann front and the expansion law; the FP32C step stays within
+    0.5 % of it in front and interface displacement, and its relative mass
+    drift within 1e-6 of the FP64 one."""
+    c = wl.three_phase(1024, 4, St=1.0)
+    kv = 1.0 - c.props.s.rho / c.props.l.rho
+    k = wl.neumann_k(1.0)
+    out = {}
+    for prec in (eulbfs.FP64, eulbfs.FP32C):
+        s = eulbfs.Solver([c], precision=prec)
+        d0 = s.diag()
+        s.step(20000)
+        out[prec] = (d0, s.diag())
+    d0, d = out[eulbfs.FP64]
+    xs = d["front_pos"]
+    assert abs(xs / (2 * k * math.sqrt(0.1 * d["t"])) - 1.0) < 0.01
+    disp = d["interface_pos"] - d0["interface_pos"]
+    assert abs(disp / (kv * xs) - 1.0) < 0.02
+    e0, e = out[eulbfs.FP32C]
+    assert abs(e["front_pos"] - xs) <= 5e-3 * xs
+    assert abs((e["interface_pos"] - e0["interface_pos"]) - disp) <= 5e-3 * abs(disp)
+    assert abs((e["mass"] / e0["mass"] - 1.0) - (d["mass"] / d0["mass"] - 1.0)) <= 1e-6
