@@ -357,3 +357,19 @@ def test_three_phase_long_run_fp32c_against_fp64():
     assert abs(e["front_pos"] - xs) <= 5e-3 * xs
     assert abs((e["interface_pos"] - e0["interface_pos"]) - disp) <= 5e-3 * abs(disp)
     assert abs((e["mass"] / e0["mass"] - 1.0) - (d["mass"] / d0["mass"] - 1.0)) <= 1e-6
+
+
+def test_film_512_long_run_fp32c_against_fp64():
+    """Liquid film freezing, 512 x 512, 5 000 steps: the FP32C step within the
+    stated FP32 tolerances of the FP64 step on the full-size film."""
+    c = wl.film(512)
+    runs = {}
+    for prec in (eulbfs.FP64, eulbfs.FP32C):
+        s = eulbfs.Solver([c], precision=prec)
+        d0 = s.diag()
+        s.step(5000)
+        runs[prec] = (s.fields(), s.diag(), d0)
+    r, dr, d0r = runs[eulbfs.FP64]
+    g, dg, d0g = runs[eulbfs.FP32C]
+    assert dr["solid_vol"] > 0 and not dr["nonfinite"]
+    check_fp32c(g, r, dg, dr, d0g, d0r)
