@@ -167,8 +167,6 @@ def domain_struct(case, keep: list) -> Domain:
     arrs = {k: np.ascontiguousarray(case.init[k], dtype=np.float64).ravel() for k in ("T", "Fl", "C", "u", "v", "p")}
     keep.append(arrs)
     init = Init(*[_ptr(arrs[k]) for k in ("T", "Fl", "C", "u", "v", "p")])
-    if abs(case.dt_stream - 0.5) > 0:
-        raise ValueError("libeulbfs uses the streaming step dt_s = 0.5 (lattice units)")
     return Domain(Grid(case.nx, case.ny), _props(case.props), _bc(case.bc), _numerics(case), init)
 
 

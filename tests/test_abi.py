@@ -93,3 +93,15 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     d = eulbfs.domain_struct(case, keep)
     assert lib.eulbfs_batch_create(1, ct.byref(d), eulbfs.FP64, None, ct.byref(h)) == eulbfs.EINVAL
     assert lib.eulbfs_step(None, 1) == eulbfs.EINVAL
+
+
+def test_streaming_steps_marshalled():
+    """A case's single streaming step stands for each distribution's step it
+    leaves unset (the oracle's convention); explicit steps win."""
+    case = wl.droplet(32)
+    case.dt_stream = 0.4
+    case.dt_f = 0.3
+    d = eulbfs.domain_struct(case, [])
+    assert (d.num.dt_stream_h, d.num.dt_stream_f, d.num.dt_stream_g) == (0.4, 0.3, 0.4)
+    d = eulbfs.domain_struct(wl.droplet(32), [])
+    assert (d.num.dt_stream_h, d.num.dt_stream_f, d.num.dt_stream_g) == (0.5, 0.5, 0.5)
