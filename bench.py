@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--impl", default="eulbfs", choices=["eulbfs", "reference"])
     ap.add_argument("--domains", type=int, default=64)
     ap.add_argument("--seed", type=int, default=4)
-    ap.add_argument("--tile", type=int, default=64, help="rows per work item (strip segment height)")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="rows per work item (strip segment height); 0: picked by eulbfs_autotune on the batch")
     ap.add_argument("--graph", type=int, default=0, help="steps per captured CUDA graph (0: direct launches)")
     ap.add_argument("--fp64-steps", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -194,7 +195,9 @@ def workload_config(cases, world: int, args) -> dict:
     return {"workload": f"static droplet freezing batch, {geo}: {len(cases)} domains per GPU, sides "
                         f"{{128,192,256,384,512}}, {cells} cells per GPU",
             "global_batch": len(cases) * world, "seq_len": cells, "parallelism": f"independent domains x{world}",
-            "precision": "FP32C", "work_item": f"31x{args.tile} strip segment", "graph_steps": args.graph,
+            "precision": "FP32C",
+            "work_item": (f"31x{args.tile} strip segment" + (" (autotuned)" if getattr(args, "autotuned", False) else ""))
+            if args.tile else "31-column strip segments, height autotuned", "graph_steps": args.graph,
             "l2": "working set > L2 (state 28 B/cell read + written per stage over 6.8 M cells)"}
 
 
@@ -246,6 +249,11 @@ def main():
     cells = sum(c.cells for c in cases)
     stream = torch.cuda.Stream()
     sol = eulbfs.Solver(cases, precision=eulbfs.FP32C, stream=stream.cuda_stream)
+    if args.tile == 0:
+        # the autotuner times each candidate height on the live batch (its
+        # steps are part of the warm-up); every solver below uses the winner
+        args.tile, _ = sol.autotune(5)
+        args.autotuned = True
     sol.set_tile(args.tile)
     if args.graph:
         sol.use_graphs(args.graph)
