@@ -17,7 +17,8 @@
  * takes the flux moments (Eq. 53), adds the cell sources (Eq. 51) and
  * advances with SSP-RK3 (Eq. 58), inverting enthalpy with Eq. 5-6.
  * Where the paper is silent or inconsistent, the reading taken is stated at
- * the code that implements it (readings R1..R23 in the design notes).
+ * the code that implements it, labelled R1, R2, ... so that the CUDA path
+ * can name the same reading.
  *
  * Units: lattice units, dx = dy = 1, lattice speed c = 1, cs^2 = 1/3.
  * Cell (i, j) has its centre at (i + 1/2, j + 1/2); arrays are row-major
