@@ -501,7 +501,7 @@ static void residual(or_solver* s, double* const W[5], double* const R[5]) {
                     rho * CS2 * kv * D;
             FE[2] = CS2 * (Fsx + rho * s->P.gx + Fix);
             FE[3] = CS2 * (Fsy + rho * s->P.gy + Fiy);
-            FE[4] = C * kv * D;                                /* R12: Eq. 47 source */
+            FE[4] = C * kv * s->dFs[c];   /* R12: Eq. 40 / 47 as printed, C (1 - rho_s/rho_l) d_t F_s */
             if (s->N.axisymmetric) {
                 /* hoop stress of the radial momentum equation, + Pi_thetatheta / r
                  * (reading R24): the pressure advanced over dt_s like the face

@@ -29,7 +29,9 @@ MUTATIONS = [
      "test_equilibria_moments"),
     ("rk3_coefficient", "0.75 * s->Wn[k][c] + 0.25 * s->W[k][c]", "0.7 * s->Wn[k][c] + 0.3 * s->W[k][c]",
      "test_rk3_mode_decay"),
-    ("phase_source_sign", "FE[4] = C * kv * D;", "FE[4] = -C * kv * D;", "test_volume_change_sources"),
+    ("phase_source_sign", "FE[4] = C * kv * s->dFs[c];", "FE[4] = -C * kv * s->dFs[c];", "test_volume_change_sources"),
+    ("phase_source_gated_twice", "FE[4] = C * kv * s->dFs[c];", "FE[4] = C * kv * D;",
+     "test_volume_change_sources_in_a_mixed_cell"),
     ("pressure_source_sign", "rho * CS2 * kv * D;\n", "- rho * CS2 * kv * D;\n", "test_volume_change_sources"),
     ("muc_sign_R5", "- s->kappa * lap;", "+ s->kappa * lap;", "test_flat_interface_equilibrium"),
     ("surface_tension_sign", "const double Fsx = -Fl * C * s->grx[P_MUC][q];",

@@ -474,12 +474,16 @@ def test_poiseuille_profile():
 #     previous-step solid fraction (R14),
 #       Eq. 27:  d(rho cs^2 u)/dt = -D (rho cs^2 u)     (F_IBM = -rho u d_t F_s)
 #       Eq. 26:  dp/dt = rho cs^2 (1 - rho_s/rho_l) D
-#       Eq. 40:  dC/dt = C (1 - rho_s/rho_l) D
-#     and SSP-RK3 multiplies a linear mode by 1 + z + z^2/2 + z^3/6.
+#       Eq. 40:  dC/dt = C (1 - rho_s/rho_l) d_t F_s
+#     and SSP-RK3 multiplies a linear mode by 1 + z + z^2/2 + z^3/6.  In a
+#     cell that is only partly condensed (C = 0.6) the rates follow the cell's
+#     solid volume D = C~ d_t F_s (reading R1) for p, while the phase field
+#     keeps Eq. 40's single factor C: the condensed volume grows by
+#     (1 - rho_s/rho_l) times the volume that froze, no more.
 # ---------------------------------------------------------------------------
-def _uniform_mushy(kv, u0, dt):
+def _uniform_mushy(kv, u0, dt, C=1.0):
     P = _props(rho=(1.0 - kv, 1.0, 1.0), L=2.0, Ts=0.0, Tl=0.0, zsv=0)
-    s = oracle.OracleSolver(_case(4, 4, P, PERIODIC_BC, T=0.0, Fl=0.5, u=u0, dt=dt))
+    s = oracle.OracleSolver(_case(4, 4, P, PERIODIC_BC, T=0.0, Fl=0.5, u=u0, dt=dt, C=C))
     st = s.state()
     st["Fsp"] = np.full_like(st["Fsp"], 0.4)           # F_s^n = 0.5, F_s^{n-1} = 0.4
     s.set_state(st, 0.0, 0)
@@ -505,6 +509,25 @@ def test_volume_change_sources():
     np.testing.assert_allclose(st["p"], st0["p"] + dt * rho * CS2 * kv * D, rtol=1e-12, atol=1e-15)
     z = kv * D * dt
     np.testing.assert_allclose(st["C"], 1.0 * (1 + z + z * z / 2 + z ** 3 / 6), rtol=1e-13)
+
+
+def test_volume_change_sources_in_a_mixed_cell():
+    dt, kv, C0 = 0.8, 0.1, 0.6
+    s, st0 = _uniform_mushy(kv, 0.0, dt, C=C0)
+    dFs = 0.1 / dt
+    s.step(1)
+    st = s.state()
+    # SSP-RK3 by hand on dC/dt = kv C dFs and dp/dt = rho(C) cs^2 kv C dFs
+    # (F_l stays 0.5: H has no source and C_p is the same in every phase)
+    src_p = lambda C: oracle.mix(s.case.props, C, 0.5, 0) * CS2 * kv * C * dFs   # noqa: E731
+    src_c = lambda C: kv * C * dFs                                             # noqa: E731
+    c1, p1 = C0 + dt * src_c(C0), dt * src_p(C0)
+    c2 = 0.75 * C0 + 0.25 * (c1 + dt * src_c(c1))
+    p2 = 0.25 * (p1 + dt * src_p(c1))
+    p3 = 2.0 / 3.0 * (p2 + dt * src_p(c2))
+    np.testing.assert_allclose(st["p"], st0["p"] + p3, rtol=1e-12)
+    z = kv * dFs * dt
+    np.testing.assert_allclose(st["C"], C0 * (1 + z + z * z / 2 + z ** 3 / 6), rtol=1e-13)
 
 
 # ---------------------------------------------------------------------------
