@@ -639,7 +639,7 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
     Rk[1] += u * (drx * cs2) + v * (dry * cs2) + rho * cs2 * K.kv * D;   // row 2
     Rk[2] += cs2 * (-Fl * C * dmx + rho * K.gx - rho * u * D);         // row 3 (R13)
     Rk[3] += cs2 * (-Fl * C * dmy + rho * K.gy - rho * v * D);         // row 4
-    Rk[4] += C * K.kv * D;                                             // row 5 (R12)
+    Rk[4] += C * K.kv * dfs;                                           // row 5 (R12: Eq. 40 / 47)
     if (AXI)   // hoop stress Pi_thetatheta / r with the pressure advanced over dt_s (reading R24)
         Rk[2] += cs2 * (PM[q].x - K.dtf * divF1 - R(2) * (&P.lm[0][0])[q].y * u * irc) * irc;
 

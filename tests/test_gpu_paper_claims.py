@@ -9,7 +9,9 @@ for 100 000 FP32C steps:
   * with solid lighter than liquid (rho_s / rho_l = 0.917) the frozen drop
     grows in height while its base radius stays, and with a denser solid
     (1.1) it shrinks in height: volume change goes mainly into the vertical
-    direction (the paper's Fig. 13 and its discussion).
+    direction (the paper's Fig. 13 and its discussion); the condensed volume
+    changes by (rho_l / rho_s - 1) times the frozen fraction, as mass
+    conservation requires.
 """
 import numpy as np
 import pytest
@@ -60,9 +62,10 @@ def test_volume_conserved_without_density_change(theta):
 def test_volume_change_goes_into_the_height(rho_sl, sign):
     d0, d, (h0, r0), (h, r) = _freeze(120.0, rho_sl)
     assert d["solid_vol"] > 0.8 * d["phase_vol"]
-    assert sign * (h / h0 - 1.0) > 0.03                             # height: +5.5 % / -7.2 % measured
+    assert sign * (h / h0 - 1.0) > 0.03                             # height: +5.0 % / -6.6 % measured
     assert abs(r / r0 - 1.0) < 0.02                                 # base radius: within 1 %
     # the condensed volume follows the density ratio on the frozen part
+    # (mass conservation; measured within 2 %)
     frozen = d["solid_vol"] / d["phase_vol"]
     expect = frozen * (1.0 / rho_sl - 1.0)
-    assert abs((d["phase_vol"] / d0["phase_vol"] - 1.0) / expect - 1.0) < 0.2
+    assert abs((d["phase_vol"] / d0["phase_vol"] - 1.0) / expect - 1.0) < 0.03
