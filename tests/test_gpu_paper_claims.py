@@ -63,7 +63,7 @@ def test_volume_change_goes_into_the_height(rho_sl, sign):
     d0, d, (h0, r0), (h, r) = _freeze(120.0, rho_sl)
     assert d["solid_vol"] > 0.8 * d["phase_vol"]
     assert sign * (h / h0 - 1.0) > 0.03                             # height: +5.0 % / -6.6 % measured
-    assert abs(r / r0 - 1.0) < 0.02                                 # base radius: within 1 %
+    assert abs(r / r0 - 1.0) < 0.02                                 # base radius: -0.04 % / -1.6 % measured
     # the condensed volume follows the density ratio on the frozen part
     # (mass conservation; measured within 2 %)
     frozen = d["solid_vol"] / d["phase_vol"]
