@@ -41,7 +41,7 @@ FP32_FLOPS_PER_CELL_STAGE = {"rz": 1142, "xy": 1100}
 WARP_INST_PER_CELL_STAGE = {"rz": 48.6, "xy": 46.3}
 # DRAM bytes per cell per launch of the stage kernel (ncu, average of the 3
 # stages of the same capture, scaled by cells).
-DRAM_BYTES_PER_CELL_LAUNCH = 64.9
+DRAM_BYTES_PER_CELL_LAUNCH = 65.0
 # FP64 operations per cell per stage of the FP64 stage kernel (DFMA counted as
 # 2), from the ncu counters of one capture of each geometry.
 FP64_FLOPS_PER_CELL_STAGE = {"rz": 1216, "xy": 1143}
