@@ -371,13 +371,15 @@ def main():
     if args.serve > 0:
         from paper_2507_03366_gb300 import serving
         from paper_2507_03366_gb300 import workloads as wl
-        reqs = wl.impact_requests(args.serve, seed=5 + 1000 * rank, axisymmetric=args.geometry == "rz")
+        reqs = wl.impact_requests(args.serve, seed=5 + 1000 * rank, axisymmetric=args.geometry == "rz",
+                                  hysteresis=True)
         rep = serving.serve(reqs, precision=eulbfs.FP32C, budget_bytes=int(args.serve_budget_gb * 2 ** 30),
                             chunk=16, stream=stream.cuda_stream, realtime=True)
         serving_out = rep.summary()
         serving_out["arrival_rate_hz"] = 20.0
         serving_out["workload"] = ("droplet impact on a cold plate, sides U[256,1024]/32, We U[10,200], "
-                                   "Re U[100,2000], St U[0.05,0.5], drop released 0.1 side above the plate, end time t U/D = 0.015")
+                                   "Re U[100,2000], St U[0.05,0.5], drop released 0.1 side above the plate, end time t U/D = 0.015, "
+                                   "plate angles theta_eq 82 / theta_adv 100 / theta_r 39 deg (hysteresis wall)")
         if fp64:
             serving_out["fp64_sequential_s_est"] = rep.cell_steps / (fp64["value"] * 1e9)
 

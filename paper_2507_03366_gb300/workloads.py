@@ -306,12 +306,14 @@ class Request:
 
 def impact_requests(n: int = 500, rate_hz: float = 20.0, seed: int = 5, lo: int = 256,
                     hi: int = 1024, U: float = 0.05, end_time_UD: float = 0.015,
-                    axisymmetric: bool = False) -> List[Request]:
+                    axisymmetric: bool = False, hysteresis: bool = False) -> List[Request]:
     """Poisson arrivals; side uniform in [lo, hi] rounded to 32; seeded We in
     [10, 200], Re in [100, 2000], St in [0.05, 0.5]; impact speed U (lattice)
     with D = side/2, rho_l/rho_g = 1000, rho_s/rho_l = 0.917.  Each request
     runs to the fixed dimensionless end time t U / D = end_time_UD (0.015 puts
-    the offered load near 0.7 of one GB300's FP32C throughput at 20/s)."""
+    the offered load near 0.7 of one GB300's FP32C throughput at 20/s).
+    hysteresis=True gives the plate the angles of Sec. 3.5 case (a):
+    theta_eq 82, theta_adv 100, theta_r 39 deg (reading R25)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     reqs = []
@@ -321,8 +323,9 @@ def impact_requests(n: int = 500, rate_hz: float = 20.0, seed: int = 5, lo: int 
         We = float(rng.uniform(10, 200))
         Re = float(rng.uniform(100, 2000))
         St = float(rng.uniform(0.05, 0.5))
-        case = droplet(side, theta_deg=90.0, St=St, rho_sl=0.917, Tw=-1.0, impact_speed=U,
-                       We=We, Re=Re, name=f"impact{k}_{side}", axisymmetric=axisymmetric)
+        case = droplet(side, theta_deg=82.0 if hysteresis else 90.0, St=St, rho_sl=0.917, Tw=-1.0, impact_speed=U,
+                       We=We, Re=Re, name=f"impact{k}_{side}", axisymmetric=axisymmetric,
+                       hysteresis=(100.0, 39.0) if hysteresis else None)
         D = 0.5 * side
         steps = max(1, int(round(end_time_UD * D / U / case.dt)))
         reqs.append(Request(k, t, case, steps))
