@@ -177,19 +177,23 @@ template <class R>
 struct FaceFlux { R Fh, Fp, Fmn, Fmt, Fc, un; };
 
 // Reconstruction pieces of one field: the cell values l, r, the face value
-// o0 (mean of the two one-sided reconstructions) and the central
+// o0 (mean of the two one-sided reconstructions l + (r - ll)/4 and
+// r - (rr - l)/4, i.e. 5/8 (l + r) - 1/8 (ll + rr)) and the central
 // t-differences dtl, dtr of the two cells (half-cell t-step = dt / 4).
 template <class R>
 struct Rec { R l, r, o0, dtl, dtr; };
+
+template <class R>
+__device__ __forceinline__ R face_value(R l, R r, R ll, R rr) {
+    return R(0.625) * (l + r) - R(0.125) * (ll + rr);
+}
 
 template <class R>
 __device__ __forceinline__ Rec<R> rec_of(R l, R r, R ll, R rr, R lp, R lm, R rp, R rm) {
     Rec<R> z;
     z.l = l;
     z.r = r;
-    const R lf = l + R(0.25) * (r - ll);
-    const R rf = r - R(0.25) * (rr - l);
-    z.o0 = R(0.5) * (lf + rf);
+    z.o0 = face_value(l, r, ll, rr);
     z.dtl = lp - lm;
     z.dtr = rp - rm;
     return z;
@@ -204,36 +208,56 @@ __device__ __forceinline__ void rec2(const P2<R>* f, const FaceIdx& x, Rec<R>& a
     b = rec_of(l.y, r.y, ll.y, rr.y, lp.y, lm.y, rp.y, rm.y);
 }
 
-// Values at the 9 points in the order 0..8 of the face frame:
-// 1, 3 cell centres; 5, 8 and 6, 7 the t-extrapolations of L and R;
-// 0 the face value; 2, 4 the face value shifted by the mean t-step.
-template <class R>
-__device__ __forceinline__ void all_points(const Rec<R>& z, R o[9]) {
-    const R st = R(0.125) * (z.dtl + z.dtr);
-    o[0] = z.o0;
-    o[1] = z.l;
-    o[2] = z.o0 - st;
-    o[3] = z.r;
-    o[4] = z.o0 + st;
-    o[5] = z.l - R(0.25) * z.dtl;
-    o[6] = z.r - R(0.25) * z.dtr;
-    o[7] = z.r + R(0.25) * z.dtr;
-    o[8] = z.l + R(0.25) * z.dtl;
-}
-
-template <class R>
-__device__ __forceinline__ R face_value(R l, R r, R ll, R rr) {
-    const R lf = l + R(0.25) * (r - ll);
-    const R rf = r - R(0.25) * (rr - l);
-    return R(0.5) * (lf + rf);
-}
-
 // Face values of both fields of a pair (cells L, R and their outer n-neighbours).
 template <class R>
 __device__ __forceinline__ void face_value2(const P2<R>* f, const FaceIdx& x, R& a, R& b) {
     const P2<R> l = f[x.L], r = f[x.R], ll = f[x.LL], rr = f[x.RR];
     a = face_value(l.x, r.x, ll.x, rr.x);
     b = face_value(l.y, r.y, ll.y, rr.y);
+}
+
+// The nonlinear parts of the equilibrium moments over the surrounding points
+// of one side column of a face: the points x_f - e_a dt_s with e_n = sn
+// (+1: the L cell, points 1, 5, 8; -1: the R cell, points 3, 6, 7).  The
+// column's centre point (e_t = 0) takes the cell values; its t-points
+// (e_t = +1 / -1) the cell value minus / plus a quarter of the central
+// t-difference.  With q = e.u + 3/2 (e.u)^2 - 1/2 u^2 (cs^2 = 1/3):
+//   centre:   q = sn u_n + u_n^2 - u_t^2 / 2
+//   t-points: q = e.u (1 + e.u) + e_n e_t u_n u_t
+// Returned: at the centre rho q, C u_n, q, C_p T q; over the t-points the sum
+// (e_t = +1 plus e_t = -1) of rho q, C e.u, q and C_p T q, and the difference
+// (+1 minus -1) of rho q and q.
+template <class R>
+struct SideSums { R f0, c0, q0, h0, fs, fd, cs, qs, qd, hs; };
+
+template <class R, int SN>
+__device__ __forceinline__ SideSums<R> side_sums(R un, R ut, R rho, R C, R T, R cp, R dun, R dut, R drho, R dC,
+                                                 R dT, R dcp) {
+    SideSums<R> s;
+    const R sun = SN > 0 ? un : -un;
+    s.q0 = fma(un, un, fma(R(-0.5) * ut, ut, sun));
+    s.f0 = rho * s.q0;
+    s.c0 = C * un;
+    s.h0 = (cp * T) * s.q0;
+    // e_t = +1: value - d/4; e_t = -1: value + d/4
+    const R unp = fma(R(-0.25), dun, un), unm = fma(R(0.25), dun, un);
+    const R utp = fma(R(-0.25), dut, ut), utm = fma(R(0.25), dut, ut);
+    const R eup = (SN > 0 ? unp : -unp) + utp;
+    const R eum = (SN > 0 ? unm : -unm) - utm;
+    const R qp = fma(SN > 0 ? unp : -unp, utp, fma(eup, eup, eup));      // e_n e_t = sn
+    const R qm = fma(SN > 0 ? -unm : unm, utm, fma(eum, eum, eum));      // e_n e_t = -sn
+    const R rp = fma(R(-0.25), drho, rho), rm = fma(R(0.25), drho, rho);
+    const R am = rm * qm;
+    s.fs = fma(rp, qp, am);
+    s.fd = fma(rp, qp, -am);
+    const R Cp_ = fma(R(-0.25), dC, C), Cm_ = fma(R(0.25), dC, C);
+    s.cs = fma(Cp_, eup, Cm_ * eum);
+    s.qs = qp + qm;
+    s.qd = qp - qm;
+    const R hp = fma(R(-0.25), dcp, cp) * fma(R(-0.25), dT, T);
+    const R hm = fma(R(0.25), dcp, cp) * fma(R(0.25), dT, T);
+    s.hs = fma(hp, qp, hm * qm);
+    return s;
 }
 
 // Sec. 2.5 steps (2)-(4) and Eq. 53 for one face.
@@ -250,7 +274,9 @@ __device__ __forceinline__ void face_value2(const P2<R>* f, const FaceIdx& x, R&
 //   mu_c part of sum g = Q ((mu_L + mu_R)/2 - mu_0), of sum e_n g = Q (mu_L - mu_R)/2
 //   C_ref T part of sum e_n h = C_ref (T_L - T_R)/6
 // (dp = central t-difference), and the nonlinear parts (rho q, C e.u,
-// C_p T q, q) are summed point by point with one multiply per weight class.
+// C_p T q, q), which are summed over the points by columns of equal e_n
+// (side_sums above, and the face column e_n = 0 below) so that each sign
+// pattern of the moments is one sum or difference of column sums.
 //
 // Axisymmetric domains (reading R24): the face pressure is advanced with the
 // axisymmetric mass source -rho cs^2 u_r / r as well, streamed with weight
@@ -260,89 +286,53 @@ __device__ __forceinline__ void face_value2(const P2<R>* f, const FaceIdx& x, R&
 template <class R, bool AXI>
 __device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const Ring<R>& P, const FaceIdx& x, bool normal_x,
                                                  bool normal_is_r, R inv_r) {
-    R un[9], ut[9], rr[9], CC[9];
-    {
-        Rec<R> ru, rv, rrho, rC;
-        rec2(&P.uv[0][0], x, ru, rv);
-        all_points(normal_x ? ru : rv, un);
-        all_points(normal_x ? rv : ru, ut);
-        rec2(&P.rc[0][0], x, rrho, rC);
-        all_points(rrho, rr);
-        all_points(rC, CC);
-    }
-    Rec<R> T, cp, p, muc;
+    Rec<R> ru, rv, rho, C, T, cp;
+    rec2(&P.uv[0][0], x, ru, rv);
+    const Rec<R>& n = normal_x ? ru : rv;         // normal velocity u_n
+    const Rec<R>& t = normal_x ? rv : ru;         // tangential velocity u_t
+    rec2(&P.rc[0][0], x, rho, C);
     rec2(&P.tc[0][0], x, T, cp);
+
+    // side columns: L (points 1, 5, 8) and R (points 3, 6, 7)
+    const SideSums<R> L = side_sums<R, 1>(n.l, t.l, rho.l, C.l, T.l, cp.l, n.dtl, t.dtl, rho.dtl, C.dtl, T.dtl, cp.dtl);
+    const SideSums<R> Rs = side_sums<R, -1>(n.r, t.r, rho.r, C.r, T.r, cp.r, n.dtr, t.dtr, rho.dtr, C.dtr, T.dtr, cp.dtr);
+
+    // face column (e_n = 0): point 0 at the face value, points 2 (e_t = +1)
+    // and 4 (e_t = -1) shifted by the mean t-step; there
+    // q = e_t u_t + u_t^2 - u_n^2 / 2, and at point 0 q = -u^2 / 2
+    const R stn = R(0.125) * (n.dtl + n.dtr), stt = R(0.125) * (t.dtl + t.dtr);
+    const R str = R(0.125) * (rho.dtl + rho.dtr), stc = R(0.125) * (C.dtl + C.dtr);
+    const R un2 = n.o0 - stn, un4 = n.o0 + stn, ut2 = t.o0 - stt, ut4 = t.o0 + stt;
+    const R q2 = fma(ut2, ut2, fma(R(-0.5) * un2, un2, ut2));
+    const R q4 = fma(ut4, ut4, fma(R(-0.5) * un4, un4, -ut4));
+    const R a4 = (rho.o0 + str) * q4;
+    const R f24s = fma(rho.o0 - str, q2, a4);     // rho q at 2 plus at 4
+    const R f24d = fma(rho.o0 - str, q2, -a4);    // rho q at 2 minus at 4
+    const R c24 = fma(C.o0 - stc, ut2, -((C.o0 + stc) * ut4));   // C e.u at 2 plus at 4
+    const R rho_f = rho.o0;
+    const R ruu0 = rho_f * fma(n.o0, n.o0, t.o0 * t.o0);       // -2 rho q at point 0
+
+    Rec<R> p, muc;
     rec2(&P.pm[0][0], x, p, muc);
-    const R mu_l = muc.l, mu_r = muc.r, mu_0 = muc.o0;
     R lamf, muf;
     face_value2(&P.lm[0][0], x, lamf, muf);
 
-    // side-point temperatures and heat capacities (e_n != 0 points only)
-    const R Ts[9] = {T.o0, T.l, R(0), T.r, R(0), T.l - R(0.25) * T.dtl, T.r - R(0.25) * T.dtr,
-                     T.r + R(0.25) * T.dtr, T.l + R(0.25) * T.dtl};
-    const R cs[9] = {cp.o0, cp.l, R(0), cp.r, R(0), cp.l - R(0.25) * cp.dtl, cp.r - R(0.25) * cp.dtr,
-                     cp.r + R(0.25) * cp.dtr, cp.l + R(0.25) * cp.dtl};
-
-    // accumulators per weight class: axis points 1-4 (w = 1/9), diagonal 5-8 (w = 1/36)
-    R fq0 = R(0);                                  // rho q at point 0 (w = 4/9)
-    R pf_a = R(0), mn_a = R(0), mt_a = R(0), pf_d = R(0), mn_d = R(0), mt_d = R(0);
-    R qn_a = R(0), qn_d = R(0), qt_d = R(0);       // sums of q for the f^eq-m moments
-    R ce_a = R(0), ce_d = R(0), cen_a = R(0), cen_d = R(0);   // C e.u and e_n C e.u
-    R th_a = R(0), th_d = R(0);                    // e_n C_p T q
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        const int en = (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
-        const int et = (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
-        const bool diag = a >= 5;
-        R eu;                                      // e.u with compile-time components of e
-        if (en != 0 && et != 0) eu = (en > 0 ? un[a] : -un[a]) + (et > 0 ? ut[a] : -ut[a]);
-        else if (en != 0) eu = en > 0 ? un[a] : -un[a];
-        else if (et != 0) eu = et > 0 ? ut[a] : -ut[a];
-        else eu = R(0);
-        const R uu = un[a] * un[a] + ut[a] * ut[a];
-        // q = cs^2 (e.u/cs^2 + (e.u)^2/(2 cs^4) - u^2/(2 cs^2)) with cs^2 = 1/3
-        const R q = (a == 0) ? R(-0.5) * uu : eu + R(1.5) * eu * eu - R(0.5) * uu;
-        const R fq = rr[a] * q;                    // non-p part of f^eq / w (Eq. 29)
-        if (a == 0) {
-            fq0 = fq;
-            continue;
-        }
-        const R ce = CC[a] * eu;                   // non-mu part of g^eq / (3 w) (Eq. 42)
-        if (!diag) {
-            pf_a += fq;
-            ce_a += ce;
-            if (en > 0) { mn_a += fq; cen_a += ce; qn_a += q; }
-            if (en < 0) { mn_a -= fq; cen_a -= ce; qn_a += q; }
-            if (et > 0) mt_a += fq;
-            if (et < 0) mt_a -= fq;
-        } else {
-            pf_d += fq;
-            ce_d += ce;
-            if (en > 0) { mn_d += fq; cen_d += ce; } else { mn_d -= fq; cen_d -= ce; }
-            if (et > 0) mt_d += fq; else mt_d -= fq;
-            qn_d += q;
-            if (en * et > 0) qt_d += q; else qt_d -= q;
-        }
-        if (en != 0) {
-            const R thq = (cs[a] * Ts[a]) * q;     // C_p T q (Eq. 9 without C_ref T)
-            if (diag) { if (en > 0) th_d += thq; else th_d -= thq; }
-            else { if (en > 0) th_a += thq; else th_a -= thq; }
-        }
-    }
-    const R w0 = R(4.0 / 9.0), w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
-    // Eq. 56 and the moments of the surrounding equilibria
-    const R pf = R(2.0 / 3.0) * p.o0 + R(1.0 / 6.0) * (p.l + p.r) + w0 * fq0 + w1 * pf_a + w5 * pf_d;
-    const R mn = R(1.0 / 6.0) * (p.l - p.r) + w1 * mn_a + w5 * mn_d;
-    const R mt = R(-1.0 / 24.0) * (p.dtl + p.dtr) + w1 * mt_a + w5 * mt_d;
-    const R Cf = CC[0] + K.Qg * (R(0.5) * (mu_l + mu_r) - mu_0) + R(1.0 / 3.0) * ce_a + R(1.0 / 12.0) * ce_d;
-    const R Sg = R(0.5) * K.Qg * (mu_l - mu_r) + R(1.0 / 3.0) * cen_a + R(1.0 / 12.0) * cen_d;
-    const R Sh = R(1.0 / 6.0) * K.Cref * (T.l - T.r) + R(1.0 / 3.0) * th_a + R(1.0 / 12.0) * th_d;
+    // Eq. 56 and the moments of the surrounding equilibria; weights 4/9, 1/9
+    // (e_n or e_t zero) and 1/36 (diagonal)
+    const R w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
+    const R pf = R(2.0 / 3.0) * p.o0 + R(1.0 / 6.0) * (p.l + p.r) - R(2.0 / 9.0) * ruu0 +
+                 w1 * ((L.f0 + Rs.f0) + f24s) + w5 * (L.fs + Rs.fs);
+    const R mn = R(1.0 / 6.0) * (p.l - p.r) + w1 * (L.f0 - Rs.f0) + w5 * (L.fs - Rs.fs);
+    const R mt = R(-1.0 / 24.0) * (p.dtl + p.dtr) + w1 * f24d + w5 * (L.fd + Rs.fd);
+    const R Cf = C.o0 + K.Qg * (R(0.5) * (muc.l + muc.r) - muc.o0) + R(1.0 / 3.0) * ((L.c0 - Rs.c0) + c24) +
+                 R(1.0 / 12.0) * (L.cs + Rs.cs);
+    const R Sg = R(0.5) * K.Qg * (muc.l - muc.r) + R(1.0 / 3.0) * (L.c0 + Rs.c0) + R(1.0 / 12.0) * (L.cs - Rs.cs);
+    const R Sh = R(1.0 / 6.0) * K.Cref * (T.l - T.r) + R(1.0 / 3.0) * (L.h0 - Rs.h0) + R(1.0 / 12.0) * (L.hs - Rs.hs);
     const R Snn_p = R(1.0 / 6.0) * (p.l + p.r);
     const R Snt_p = R(1.0 / 72.0) * (p.dtr - p.dtl);
-    const R Snn_q = w1 * qn_a + w5 * qn_d;
-    const R Snt_q = w5 * qt_d;
+    const R Snn_q = w1 * (L.q0 + Rs.q0) + w5 * (L.qs + Rs.qs);
+    const R Snt_q = w5 * (L.qd - Rs.qd);
     // rho_f cs^2 u_f = sum e f^eq (Eq. 56); tau from the face properties (R9)
-    const R rho_f = rr[0];
     const R irf = wdiv(R(1), rho_f);
     const R unf = R(3) * mn * irf, utf = R(3) * mt * irf;
     const R th = K.six_over_Cref * lamf * irf;   // tau_h - 0.5 = lambda / (rho C_ref cs^2 dt_s)
@@ -358,7 +348,7 @@ __device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const Ring<
     F.Fmt = (R(1) - tf) * cs2 * rho_f * unf * utf + tf * (Snt_p + rho_f * Snt_q);
     F.Fc = (R(1) - tg) * Cf * unf + tg * Sg;     // Eq. 44, 46
     F.un = unf;
-    if (AXI) F.Fmn += R(-1.0 / 18.0) * rho_f * (normal_is_r ? un[0] : ut[0]) * inv_r;
+    if (AXI) F.Fmn += R(-1.0 / 18.0) * rho_f * (normal_is_r ? n.o0 : t.o0) * inv_r;
     return F;
 }
 
