@@ -63,12 +63,22 @@ __device__ __forceinline__ float wdiv(float a, float b) { return __fdividef(a, b
 // Eq. 5-6 with the readings of the oracle: uniform latent heat, Eq. 7 mixture
 // heat capacity gated by clamp(C).  H = Hh + Hl (Hl = 0 in FP64); the
 // differences H - H_s and H - H_l are formed from the pair without rounding H.
+// A constant group (Q4) of Consts: one 16-byte load in FP32.
+template <class R>
+__device__ __forceinline__ Q4<R> ld4(const Q4<R>& q) { return q; }
+template <>
+__device__ __forceinline__ Q4<float> ld4(const Q4<float>& q) {
+    const float4 v = *reinterpret_cast<const float4*>(&q);
+    return Q4<float>{v.x, v.y, v.z, v.w};
+}
+
 template <class R>
 __device__ __forceinline__ void invert_enthalpy(const Consts<R>& K, R Hh, R Hl, R Ct, R& T, R& Fl) {
-    const R cps = Ct * K.cp[0] + (R(1) - Ct) * K.cp[2];
-    const R cpl = Ct * K.cp[1] + (R(1) - Ct) * K.cp[2];
-    const R Hs = cps * K.Ts;
-    const R HL = cpl * K.Tl + K.L;
+    const Q4<R> cp = ld4(K.mcp), e = ld4(K.enth);
+    const R cps = fma(Ct, cp.y, cp.x);     // C~ cp_s + (1 - C~) cp_g
+    const R cpl = fma(Ct, cp.w, cp.x);     // C~ cp_l + (1 - C~) cp_g
+    const R Hs = cps * e.x;
+    const R HL = fma(cpl, e.y, e.z);
     const R ds = (Hh - Hs) + Hl;
     const R dl = (Hh - HL) + Hl;
     if (ds < R(0)) {
@@ -76,20 +86,21 @@ __device__ __forceinline__ void invert_enthalpy(const Consts<R>& K, R Hh, R Hl, 
         T = wdiv(Hh + Hl, cps);
     } else if (dl > R(0)) {
         Fl = R(1);
-        T = K.Tl + wdiv(dl, cpl);
+        T = e.y + wdiv(dl, cpl);
     } else if (HL > Hs) {
         Fl = wdiv(ds, HL - Hs);
-        T = K.Ts + Fl * (K.Tl - K.Ts);
+        T = fma(Fl, e.w, e.x);
     } else {
         Fl = R(1);
-        T = K.Tl;
+        T = e.y;
     }
 }
 
-// Eq. 7 (reading R1): gamma = C~ [F_s g_s + F_l g_l] + (1 - C~) g_g.
+// Eq. 7 (reading R1): gamma = C~ [F_s g_s + F_l g_l] + (1 - C~) g_g, as
+// g_g + C~ ((g_s - g_g) + F_l (g_l - g_s)) from the property's group.
 template <class R>
-__device__ __forceinline__ R mix(R Ct, R Fl, const R g[3]) {
-    return Ct * ((R(1) - Fl) * g[0] + Fl * g[1]) + (R(1) - Ct) * g[2];
+__device__ __forceinline__ R mix(R Ct, R Fl, const Q4<R>& m) {
+    return fma(Ct, fma(Fl, m.z, m.y), m.x);
 }
 
 // Map a cell coordinate outside [0, n) through its boundary: periodic wrap or
@@ -177,10 +188,10 @@ __device__ __forceinline__ Prim<R> derive(const Consts<R>& K, const SV<R>& w) {
     const R C = w.Ch + w.Cl;
     const R Ct = clamp01(C);
     invert_enthalpy(K, w.Hh, w.Hl, Ct, q.T, q.Fl);
-    q.cp = mix(Ct, q.Fl, K.cp);
-    q.rho = mix(Ct, q.Fl, K.rho);
-    q.lam = mix(Ct, q.Fl, K.lam);
-    q.mu = mix(Ct, q.Fl, K.mu);
+    q.cp = mix(Ct, q.Fl, ld4(K.mcp));
+    q.rho = mix(Ct, q.Fl, ld4(K.mrho));
+    q.lam = mix(Ct, q.Fl, ld4(K.mlam));
+    q.mu = mix(Ct, q.Fl, ld4(K.mmu));
     const R r3 = wdiv(R(3), q.rho);     // 1 / (rho cs^2)
     q.u = w.mx * r3;
     q.v = w.my * r3;

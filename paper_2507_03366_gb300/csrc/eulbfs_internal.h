@@ -43,11 +43,21 @@ struct DomainDesc {
     long long plane;         // nx * ny
 };
 
+// Four constants that the kernels read together: one 16-byte shared-memory
+// load in FP32 (two in FP64) instead of four.
+template <class R>
+struct alignas(16) Q4 { R x, y, z, w; };
+
 // Working-precision copy of a domain's constants.  Built on the host for the
 // stage kernel (one per domain, copied into shared memory per work item) and
 // on the device by the auxiliary kernels.
 template <class R>
 struct Consts {
+    // groups read with one load (Q4): Eq. 7 mixtures of C_p, rho, lambda, mu
+    // as {g_g, g_s - g_g, g_l - g_s, g_l - g_g}; {T_s, T_l, L, T_l - T_s};
+    // face {Q, C_ref / 6, 6 / C_ref, tau_g - 1/2}; cell {kv, g_x, g_y, 1 / dt}
+    // and {2 beta, kappa, dt, dt_f}
+    Q4<R> mcp, mrho, mlam, mmu, enth, facec, cellc, cellc2;
     R rho[3], mu[3], lam[3], cp[3];
     R L, Ts, Tl, beta, kappa, Qg, tau_g, Cref, kv, gx, gy, dt;
     R six_over_Cref, inv_dt;   // 6 / C_ref = 1 / (C_ref cs^2 dt_s), 1 / dt
@@ -67,7 +77,28 @@ struct Consts {
 };
 
 template <class R>
+__host__ __device__ inline Q4<R> make_q4(double x, double y, double z, double w) {
+    Q4<R> q;
+    q.x = (R)x; q.y = (R)y; q.z = (R)z; q.w = (R)w;
+    return q;
+}
+
+// {g_g, g_s - g_g, g_l - g_s, g_l - g_g} of one property (solid, liquid, gas)
+template <class R>
+__host__ __device__ inline Q4<R> mixture_q4(const double g[3]) {
+    return make_q4<R>(g[2], g[0] - g[2], g[1] - g[0], g[1] - g[2]);
+}
+
+template <class R>
 __host__ __device__ inline void fill_consts(const DomainDesc& d, Consts<R>& K) {
+    K.mcp = mixture_q4<R>(d.cp);
+    K.mrho = mixture_q4<R>(d.rho);
+    K.mlam = mixture_q4<R>(d.lam);
+    K.mmu = mixture_q4<R>(d.mu);
+    K.enth = make_q4<R>(d.Ts, d.Tl, d.L, d.Tl - d.Ts);
+    K.facec = make_q4<R>(d.Qg, d.Cref / 6.0, 6.0 / d.Cref, d.tau_g - 0.5);
+    K.cellc = make_q4<R>(d.kv, d.gx, d.gy, 1.0 / d.dt);
+    K.cellc2 = make_q4<R>(2.0 * d.beta, d.kappa, d.dt, d.dts[1]);
     for (int k = 0; k < 3; ++k) {
         K.rho[k] = (R)d.rho[k]; K.mu[k] = (R)d.mu[k]; K.lam[k] = (R)d.lam[k]; K.cp[k] = (R)d.cp[k];
     }

@@ -45,7 +45,7 @@ __global__ void init_kernel(const DomainDesc* dd, const double* T, const double*
         const double H = enthalpy_of(Kd, T[c], Fl ? Fl[c] : 1.0, Cc);
         double Td, Fld;
         invert_enthalpy(Kd, H, 0.0, clamp01(Cc), Td, Fld);
-        const double rho = mix(clamp01(Cc), Fld, Kd.rho);
+        const double rho = mix(clamp01(Cc), Fld, Kd.mrho);
         SV<R> s;
         if (sizeof(R) == 8) { s.Hh = (R)H; s.Hl = 0; s.Ch = (R)Cc; s.Cl = 0; }
         else { put_pair(s.Hh, s.Hl, H); put_pair(s.Ch, s.Cl, Cc); }
@@ -73,7 +73,7 @@ __global__ void fields_kernel(const DomainDesc* dd, long long n, double* H, doub
         const double Hd = pair_value(w.Hh, w.Hl), Cd = pair_value(w.Ch, w.Cl);
         double Td, Fld;
         invert_enthalpy(Kd, Hd, 0.0, clamp01(Cd), Td, Fld);
-        const double rho = mix(clamp01(Cd), Fld, Kd.rho);
+        const double rho = mix(clamp01(Cd), Fld, Kd.mrho);
         if (H) H[c] = Hd;
         if (T) T[c] = Td;
         if (Fl) Fl[c] = Fld;
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kDiagThreads) diag_partial_kernel(const Domain
         const double H = pair_value(w.Hh, w.Hl), C = pair_value(w.Ch, w.Cl);
         double T, Fl;
         invert_enthalpy(Kd, H, 0.0, clamp01(C), T, Fl);
-        const double rho = mix(clamp01(C), Fl, Kd.rho);
+        const double rho = mix(clamp01(C), Fl, Kd.mrho);
         // cell volume: 1, or the radius r_i = i + 1/2 per radian (axisymmetric)
         const double vol = Kd.axi ? (double)(c % Kd.nx) + 0.5 : 1.0;
         acc[0] += vol * rho;
@@ -273,7 +273,7 @@ diag_partial_noalloc_kernel(Consts<double> Kd, const R* b, long long n, double* 
         const double H = pair_value(w.Hh, w.Hl), C = pair_value(w.Ch, w.Cl);
         double T, Fl;
         invert_enthalpy(Kd, H, 0.0, clamp01(C), T, Fl);
-        const double rho = mix(clamp01(C), Fl, Kd.rho);
+        const double rho = mix(clamp01(C), Fl, Kd.mrho);
         acc[0] += rho;
         acc[1] += H;
         acc[2] += C;
@@ -341,13 +341,20 @@ extern "C" int eulbfs_diagnostics_noalloc(int precision, const void* state, int 
     double* scratch = nullptr;
     int rc = noalloc_scratch(&scratch);
     if (rc != EULBFS_OK) return rc;
-    Consts<double> Kd = {};
+    // the constants the closure and the integrals use (Eq. 5-7), as the
+    // other entry points fill them
+    DomainDesc d = {};
     const eulbfs_phase* ph[3] = {&props->s, &props->l, &props->g};
-    for (int k = 0; k < 3; ++k) { Kd.rho[k] = ph[k]->rho; Kd.cp[k] = ph[k]->cp; }
-    Kd.Ts = props->Ts;
-    Kd.Tl = props->Tl;
-    Kd.L = props->L;
-    Kd.plane = n;
+    for (int k = 0; k < 3; ++k) { d.rho[k] = ph[k]->rho; d.cp[k] = ph[k]->cp; }
+    d.Ts = props->Ts;
+    d.Tl = props->Tl;
+    d.L = props->L;
+    d.Cref = 1.0;
+    d.dt = 1.0;
+    d.dts[0] = d.dts[1] = d.dts[2] = 0.5;
+    d.plane = n;
+    Consts<double> Kd = {};
+    fill_consts(d, Kd);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (precision == EULBFS_FP64)
         diag_partial_noalloc_kernel<double><<<nb, kDiagThreads, 0, s>>>(Kd, static_cast<const double*>(state), n, scratch);

@@ -124,7 +124,8 @@ __device__ __forceinline__ R chem_potential(const Consts<R>& K, const P2<R>* RC,
     } else {
         lap = ce + cw + cn + cs - R(4) * c;
     }
-    return R(2) * K.beta * c * (c - R(1)) * (R(2) * c - R(1)) - K.kappa * lap;
+    const Q4<R> cc = ld4(K.cellc2);   // 2 beta, kappa
+    return cc.x * c * (c - R(1)) * (R(2) * c - R(1)) - cc.y * lap;
 }
 
 // Step 2: mu_c for rows [r0, r0 + nrows), columns 1 .. RW-2.  A wall ghost
@@ -316,6 +317,7 @@ __device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const Ring<
     rec2(&P.pm[0][0], x, p, muc);
     R lamf, muf;
     face_value2(&P.lm[0][0], x, lamf, muf);
+    const Q4<R> fc = ld4(K.facec);   // Q, C_ref / 6, 6 / C_ref, tau_g - 1/2
 
     // Eq. 56 and the moments of the surrounding equilibria; weights 4/9, 1/9
     // (e_n or e_t zero) and 1/36 (diagonal)
@@ -324,10 +326,10 @@ __device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const Ring<
                  w1 * ((L.f0 + Rs.f0) + f24s) + w5 * (L.fs + Rs.fs);
     const R mn = R(1.0 / 6.0) * (p.l - p.r) + w1 * (L.f0 - Rs.f0) + w5 * (L.fs - Rs.fs);
     const R mt = R(-1.0 / 24.0) * (p.dtl + p.dtr) + w1 * f24d + w5 * (L.fd + Rs.fd);
-    const R Cf = C.o0 + K.Qg * (R(0.5) * (muc.l + muc.r) - muc.o0) + R(1.0 / 3.0) * ((L.c0 - Rs.c0) + c24) +
+    const R Cf = C.o0 + fc.x * (R(0.5) * (muc.l + muc.r) - muc.o0) + R(1.0 / 3.0) * ((L.c0 - Rs.c0) + c24) +
                  R(1.0 / 12.0) * (L.cs + Rs.cs);
-    const R Sg = R(0.5) * K.Qg * (muc.l - muc.r) + R(1.0 / 3.0) * (L.c0 + Rs.c0) + R(1.0 / 12.0) * (L.cs - Rs.cs);
-    const R Sh = R(1.0 / 6.0) * K.Cref * (T.l - T.r) + R(1.0 / 3.0) * (L.h0 - Rs.h0) + R(1.0 / 12.0) * (L.hs - Rs.hs);
+    const R Sg = R(0.5) * fc.x * (muc.l - muc.r) + R(1.0 / 3.0) * (L.c0 + Rs.c0) + R(1.0 / 12.0) * (L.cs - Rs.cs);
+    const R Sh = fc.y * (T.l - T.r) + R(1.0 / 3.0) * (L.h0 - Rs.h0) + R(1.0 / 12.0) * (L.hs - Rs.hs);
     const R Snn_p = R(1.0 / 6.0) * (p.l + p.r);
     const R Snt_p = R(1.0 / 72.0) * (p.dtr - p.dtl);
     const R Snn_q = w1 * (L.q0 + Rs.q0) + w5 * (L.qs + Rs.qs);
@@ -335,9 +337,9 @@ __device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const Ring<
     // rho_f cs^2 u_f = sum e f^eq (Eq. 56); tau from the face properties (R9)
     const R irf = wdiv(R(1), rho_f);
     const R unf = R(3) * mn * irf, utf = R(3) * mt * irf;
-    const R th = K.six_over_Cref * lamf * irf;   // tau_h - 0.5 = lambda / (rho C_ref cs^2 dt_s)
+    const R th = fc.z * lamf * irf;              // tau_h - 0.5 = lambda / (rho C_ref cs^2 dt_s)
     const R tf = R(6) * muf * irf;               // tau_f - 0.5 = mu / (rho cs^2 dt_s)
-    const R tg = K.tau_g - R(0.5);
+    const R tg = fc.w;
     const R cs2 = R(1.0 / 3.0);
     FaceFlux<R> F;
     // h* = (1.5 - tau) h^eq(x_f) + (tau - 0.5) h^eq(x_f - e dt_s) (Eq. 13, 16)
@@ -613,11 +615,12 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
     const R dry = R(0.5) * (RC[qn].x - RC[qs].x);
     const R dmx = R(0.5) * (PM[q + 1].y - PM[q - 1].y);
     const R dmy = R(0.5) * (PM[qn].y - PM[qs].y);
+    const Q4<R> cc = ld4(K.cellc);   // kv, g_x, g_y, 1 / dt
     R dfs;
     if (stage == 0) {   // reading R14: lagged dF_s/dt, fixed over the step
         R* Fsp = reinterpret_cast<R*>(K.Fsp);
         const R Fs = R(1) - Fl;
-        dfs = (Fs - Fsp[c]) * K.inv_dt;
+        dfs = (Fs - Fsp[c]) * cc.w;
         reinterpret_cast<R*>(K.dFs)[c] = dfs;
         Fsp[c] = Fs;
     } else {
@@ -626,12 +629,13 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
     const R cs2 = R(1.0 / 3.0);
     const R D = clamp01(C) * dfs;
     Rk[0] += Cp * T * divu;                                           // Eq. 51 row 1
-    Rk[1] += u * (drx * cs2) + v * (dry * cs2) + rho * cs2 * K.kv * D;   // row 2
-    Rk[2] += cs2 * (-Fl * C * dmx + rho * K.gx - rho * u * D);         // row 3 (R13)
-    Rk[3] += cs2 * (-Fl * C * dmy + rho * K.gy - rho * v * D);         // row 4
-    Rk[4] += C * K.kv * dfs;                                           // row 5 (R12: Eq. 40 / 47)
+    Rk[1] += u * (drx * cs2) + v * (dry * cs2) + rho * cs2 * cc.x * D;   // row 2
+    Rk[2] += cs2 * (-Fl * C * dmx + rho * cc.y - rho * u * D);         // row 3 (R13)
+    Rk[3] += cs2 * (-Fl * C * dmy + rho * cc.z - rho * v * D);         // row 4
+    Rk[4] += C * cc.x * dfs;                                           // row 5 (R12: Eq. 40 / 47)
+    const Q4<R> c2 = ld4(K.cellc2);   // dt, dt_f in z, w
     if (AXI)   // hoop stress Pi_thetatheta / r with the pressure advanced over dt_s (reading R24)
-        Rk[2] += cs2 * (PM[q].x - K.dtf * divF1 - R(2) * (&P.lm[0][0])[q].y * u * irc) * irc;
+        Rk[2] += cs2 * (PM[q].x - c2.w * divF1 - R(2) * (&P.lm[0][0])[q].y * u * irc) * irc;
 
     // stage 0 reads W^n as its input: one load serves both
     const SV<R> wn = load_state(reinterpret_cast<const R*>(K.st[0]), K.plane, c);
@@ -641,7 +645,7 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
         // Eq. 58 as written
         const R A = stage == 0 ? R(1) : (stage == 1 ? R(0.75) : R(1.0 / 3.0));
         const R B = stage == 0 ? R(0) : (stage == 1 ? R(0.25) : R(2.0 / 3.0));
-        const R Cd = (stage == 0 ? R(1) : (stage == 1 ? R(0.25) : R(2.0 / 3.0))) * K.dt;
+        const R Cd = (stage == 0 ? R(1) : (stage == 1 ? R(0.25) : R(2.0 / 3.0))) * c2.z;
         o.Hh = A * wn.Hh + B * ws.Hh + Cd * Rk[0];
         o.p = A * wn.p + B * ws.p + Cd * Rk[1];
         o.mx = A * wn.mx + B * ws.mx + Cd * Rk[2];
@@ -653,7 +657,7 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
         // Eq. 58 as W^n + increment; H and C kept as compensated pairs.  TwoSum
         // for the sum and the renormalisation keeps every pair canonical.
         const R B = stage == 0 ? R(0) : (stage == 1 ? R(0.25) : R(2.0 / 3.0));
-        const R Cd = (stage == 0 ? R(1) : (stage == 1 ? R(0.25) : R(2.0 / 3.0))) * K.dt;
+        const R Cd = (stage == 0 ? R(1) : (stage == 1 ? R(0.25) : R(2.0 / 3.0))) * c2.z;
         const R dH = B * ((ws.Hh - wn.Hh) + (ws.Hl - wn.Hl)) + Cd * Rk[0];
         const R dC = B * ((ws.Ch - wn.Ch) + (ws.Cl - wn.Cl)) + Cd * Rk[4];
         R s1, e1;
