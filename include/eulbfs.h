@@ -270,9 +270,12 @@ int eulbfs_diagnostics_noalloc(int precision, const void* state, int nx, int ny,
 
 /* Pick the work-item height of the current batch by timing each candidate
  * (16, 32, 64, 128, 256 rows) over steps_per_candidate steps on the solver's
- * stream and keeping the fastest.  The timed steps are real steps of every
+ * stream, in two rounds, and keeping the candidate with the fastest of its
+ * two timings (*best_ms_per_step).  The timed steps are real steps of every
  * active domain (results do not depend on the height), so the simulation
- * advances by 5 * (steps_per_candidate + 1) steps.  Synchronises the stream. */
+ * advances by 2 * 5 * (steps_per_candidate + 1) steps.  Synchronises the
+ * stream.  EULBFS_EINVAL for a null solver or steps_per_candidate < 1; a
+ * failing step returns its error and leaves the height unchanged. */
 int eulbfs_autotune(eulbfs_solver* s, int steps_per_candidate, int* best_rows, float* best_ms_per_step);
 
 void eulbfs_destroy(eulbfs_solver* s);

@@ -504,30 +504,41 @@ int eulbfs_autotune(eulbfs_solver* s, int steps_per_candidate, int* best_rows, f
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0), "event");
     CK(cudaEventCreate(&e1), "event");
-    const int saved_graph = s->graph_steps;
+    const int saved_graph = s->graph_steps, saved_seg = s->seg;
     s->graph_steps = 0;                      // time the launches themselves
+    constexpr int kNC = (int)(sizeof(kCandidates) / sizeof(kCandidates[0]));
+    constexpr int kRounds = 2;               // each candidate's best of two rounds
+    float cand_ms[kNC] = {};
     int best = s->seg;
     float best_ms = 0.f;
     int rc = EULBFS_OK;
-    for (int rows : kCandidates) {
-        rc = eulbfs_set_tile(s, rows);
-        if (rc == EULBFS_OK) rc = eulbfs_step(s, 1);   // rebuild + warm the work list
-        if (rc != EULBFS_OK) break;
-        if (s->nitems == 0) break;                     // nothing to time
-        cudaEventRecord(e0, s->stream);
-        rc = eulbfs_step(s, steps_per_candidate);
-        cudaEventRecord(e1, s->stream);
-        if (rc != EULBFS_OK) break;
-        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "autotune timing"); break; }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= steps_per_candidate;
-        if (best_ms == 0.f || ms < best_ms) { best_ms = ms; best = rows; }
+    for (int round = 0; round < kRounds && rc == EULBFS_OK; ++round) {
+        for (int k = 0; k < kNC; ++k) {
+            rc = eulbfs_set_tile(s, kCandidates[k]);
+            if (rc == EULBFS_OK) rc = eulbfs_step(s, 1);   // rebuild + warm the work list
+            if (rc != EULBFS_OK) break;
+            if (s->nitems == 0) break;                     // nothing to time
+            cudaEventRecord(e0, s->stream);
+            rc = eulbfs_step(s, steps_per_candidate);
+            cudaEventRecord(e1, s->stream);
+            if (rc != EULBFS_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "autotune timing"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= steps_per_candidate;
+            if (cand_ms[k] == 0.f || ms < cand_ms[k]) cand_ms[k] = ms;
+        }
     }
+    for (int k = 0; k < kNC; ++k)
+        if (cand_ms[k] > 0.f && (best_ms == 0.f || cand_ms[k] < best_ms)) { best_ms = cand_ms[k]; best = kCandidates[k]; }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     s->graph_steps = saved_graph;
-    if (rc != EULBFS_OK) return rc;
+    if (rc != EULBFS_OK) {
+        const std::string msg = eulbfs_last_error();   // the step's error, kept over the restore
+        eulbfs_set_tile(s, saved_seg);
+        return fail(rc, msg.c_str());
+    }
     eulbfs_set_tile(s, best);
     if (best_rows) *best_rows = best;
     if (best_ms_per_step) *best_ms_per_step = best_ms;

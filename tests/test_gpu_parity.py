@@ -263,6 +263,22 @@ def test_graph_replay_and_work_item_shapes_bitwise(precision):
                 assert np.array_equal(s.fields(k)[f], ref.fields(k)[f]), (tile, k, f)
 
 
+def test_autotune_picks_a_candidate_and_steps_as_documented():
+    cases = wl.static_droplet_batch(3, sides=(40, 72), axisymmetric=True)
+    s = eulbfs.Solver(cases, precision=eulbfs.FP32C)
+    rows, ms = s.autotune(2)
+    assert rows in (16, 32, 64, 128, 256) and ms > 0
+    steps = 2 * 5 * (2 + 1)               # two rounds over five heights, each 1 + 2 steps
+    assert s.diag(0)["step"] == steps
+    ref = eulbfs.Solver(cases, precision=eulbfs.FP32C)
+    ref.step(steps)
+    for k in range(3):                    # the heights it ran do not change the result
+        for f in FIELDS:
+            assert np.array_equal(s.fields(k)[f], ref.fields(k)[f]), (k, f)
+    with pytest.raises(eulbfs.EulbfsError):
+        s.autotune(0)
+
+
 # ---------------------------------------------------------------------------
 # Continuous batching and failure detection (host-side faults only).
 # ---------------------------------------------------------------------------
