@@ -17,6 +17,7 @@ workload instead.
 from __future__ import annotations
 
 import argparse
+import copy
 import json
 import os
 import statistics
@@ -45,6 +46,8 @@ DRAM_BYTES_PER_CELL_LAUNCH = 65.1
 # FP64 operations per cell per stage of the FP64 stage kernel (DFMA counted as
 # 2), from the ncu counters of one capture of each geometry.
 FP64_FLOPS_PER_CELL_STAGE = {"rz": 1035, "xy": 958}
+# Streaming steps (dt_h, dt_f, dt_g) of the general-face-path leg.
+GEN_STEPS = (0.3, 0.4, 0.3)
 # Peaks from unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x SM clock;
 # 4 warp instructions issued per SM per clock (one per scheduler); 2 FP64
 # FMA lanes per SM (ncu's sustained DFMA peak) x 2 flops x SM clock.
@@ -63,6 +66,8 @@ def parse():
                     help="rows per work item (strip segment height); 0: picked by eulbfs_autotune on the batch")
     ap.add_argument("--graph", type=int, default=0, help="steps per captured CUDA graph (0: direct launches)")
     ap.add_argument("--fp64-steps", type=int, default=30)
+    ap.add_argument("--gen-steps", type=int, default=200,
+                    help="steps of the general-streaming-step leg (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve", type=int, default=200, help="requests in the serving leg (0: skip)")
@@ -338,6 +343,32 @@ def main():
                                 "peak_source": "unit counts x max SM clock (152 x 2 x 2 x %.0f MHz)" % clk_mhz}
         s64.close()
 
+    # ---- the same batch with per-distribution streaming steps (reading R26) ----
+    # dt_h = dt_g = 0.3, dt_f = 0.4: every domain takes the general face path
+    gen = None
+    if args.gen_steps > 0:
+        gcases = []
+        for c in cases:
+            g = copy.copy(c)
+            g.dt_h, g.dt_f, g.dt_g = GEN_STEPS
+            gcases.append(g)
+        sg = eulbfs.Solver(gcases, precision=eulbfs.FP32C, stream=stream.cuda_stream)
+        sg.set_tile(args.tile)
+        sg.step(3)
+        sg.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sg.step(args.gen_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msg = e0.elapsed_time(e1)
+        gv = cells * args.gen_steps / (msg * 1e-3) / 1e9
+        gen = {"value": gv, "unit": "GCUPS", "steps": args.gen_steps, "ms_per_step": msg / args.gen_steps,
+               "dt_stream_hfg": list(GEN_STEPS),
+               "relative_to_half_step_path": gv / (cells * args.steps / (ms * 1e-3) / 1e9),
+               "nonfinite": any(sg.diag(k)["nonfinite"] for k in range(len(gcases)))}
+        sg.close()
+
     # ---- end to end through the public API with host buffers -------------------
     e2e = None
     if not args.no_e2e:
@@ -407,6 +438,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": launches,
         "fp64_plain": fp64,
+        "general_streaming": gen,
         "serving": serving_out,
         "clocks": clk,
     }

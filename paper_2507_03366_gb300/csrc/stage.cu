@@ -389,132 +389,161 @@ __device__ __forceinline__ void recn2(const P2<R>* f, const FaceIdx& x, RecN<R>&
     b = recn_of(l.y, r.y, ll.y, rr.y, lp.y, lm.y, rp.y, rm.y);
 }
 
-// Values at the 9 points x_f - e_a dt (order as in all_points); a = 1/2 - dt.
-template <class R>
-__device__ __forceinline__ void points_dt(const RecN<R>& z, R dt, R o[9]) {
-    const R a = R(0.5) - dt, b = R(0.5) * dt;
-    const R lp = z.l + a * z.gl, rp = z.r - a * z.gr;
-    const R st = R(0.5) * b * (z.dtl + z.dtr);
-    o[0] = z.o0;
-    o[1] = lp;
-    o[2] = z.o0 - st;
-    o[3] = rp;
-    o[4] = z.o0 + st;
-    o[5] = lp - b * z.dtl;
-    o[6] = rp - b * z.dtr;
-    o[7] = rp + b * z.dtr;
-    o[8] = lp + b * z.dtl;
+// q at the centre of a side column (e_n = SN, e_t = 0) and at its t-points
+// (e_t = +1: value - d, e_t = -1: value + d), with e.u at the t-points; the
+// forms of side_sums above.
+template <class R, int SN>
+__device__ __forceinline__ R q_centre(R un, R ut) {
+    return fma(un, un, fma(R(-0.5) * ut, ut, SN > 0 ? un : -un));
 }
 
-__device__ __forceinline__ int e_n(int a) { return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0); }
-__device__ __forceinline__ int e_t(int a) { return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0); }
+template <class R, int SN>
+__device__ __forceinline__ void eu_tpoints(R un, R ut, R dun, R dut, R& unp, R& utp, R& unm, R& utm, R& eup, R& eum) {
+    unp = un - dun; unm = un + dun; utp = ut - dut; utm = ut + dut;
+    eup = (SN > 0 ? unp : -unp) + utp;
+    eum = (SN > 0 ? unm : -unm) - utm;
+}
 
+template <class R, int SN>
+__device__ __forceinline__ void q_tpoints(R un, R ut, R dun, R dut, R& qp, R& qm) {
+    R unp, utp, unm, utm, eup, eum;
+    eu_tpoints<R, SN>(un, ut, dun, dut, unp, utp, unm, utm, eup, eum);
+    qp = fma(SN > 0 ? unp : -unp, utp, fma(eup, eup, eup));      // e_n e_t = SN
+    qm = fma(SN > 0 ? -unm : unm, utm, fma(eum, eum, eum));      // e_n e_t = -SN
+}
+
+// The value of one field at the centre of a side column for a streaming step
+// with a = 1/2 - dt: the L cell's f + a g_n, the R cell's f - a g_n.
+template <class R, int SN>
+__device__ __forceinline__ R col_centre(const RecN<R>& z, R a) {
+    return SN > 0 ? fma(a, z.gl, z.l) : fma(-a, z.gr, z.r);
+}
+template <class R, int SN>
+__device__ __forceinline__ R col_dt(const RecN<R>& z) { return SN > 0 ? z.dtl : z.dtr; }
+
+// f (points at dt_f): rho q and q of one side column; sums and differences
+// over the t-points as in side_sums.
 template <class R>
-__device__ __forceinline__ R e_dot(int a, R un, R ut) {
-    const int en = e_n(a), et = e_t(a);
-    return (en == 0 ? R(0) : (en > 0 ? un : -un)) + (et == 0 ? R(0) : (et > 0 ? ut : -ut));
+struct ColF { R f0, q0, fs, fd, qs, qd; };
+
+template <class R, int SN>
+__device__ __forceinline__ ColF<R> col_f(const RecN<R>& Un, const RecN<R>& Ut, const RecN<R>& Rho, R a, R b) {
+    ColF<R> s;
+    const R un = col_centre<R, SN>(Un, a), ut = col_centre<R, SN>(Ut, a), rho = col_centre<R, SN>(Rho, a);
+    s.q0 = q_centre<R, SN>(un, ut);
+    s.f0 = rho * s.q0;
+    R qp, qm;
+    q_tpoints<R, SN>(un, ut, b * col_dt<R, SN>(Un), b * col_dt<R, SN>(Ut), qp, qm);
+    const R dr = b * col_dt<R, SN>(Rho);
+    const R am = (rho + dr) * qm;
+    s.fs = fma(rho - dr, qp, am);
+    s.fd = fma(rho - dr, qp, -am);
+    s.qs = qp + qm;
+    s.qd = qp - qm;
+    return s;
+}
+
+// g (points at dt_g): C u_n at the centre and the t-points' sum of C e.u.
+template <class R, int SN>
+__device__ __forceinline__ void col_g(const RecN<R>& Un, const RecN<R>& Ut, const RecN<R>& Cc, R a, R b, R& c0, R& cs) {
+    const R un = col_centre<R, SN>(Un, a), ut = col_centre<R, SN>(Ut, a), C = col_centre<R, SN>(Cc, a);
+    c0 = C * un;
+    R unp, utp, unm, utm, eup, eum;
+    eu_tpoints<R, SN>(un, ut, b * col_dt<R, SN>(Un), b * col_dt<R, SN>(Ut), unp, utp, unm, utm, eup, eum);
+    const R dC = b * col_dt<R, SN>(Cc);
+    cs = fma(C - dC, eup, (C + dC) * eum);
+}
+
+// h (points at dt_h): C_p T q at the centre and the t-points' sum.
+template <class R, int SN>
+__device__ __forceinline__ void col_h(const RecN<R>& Un, const RecN<R>& Ut, const RecN<R>& T, const RecN<R>& cp, R a,
+                                      R b, R& h0, R& hs) {
+    const R un = col_centre<R, SN>(Un, a), ut = col_centre<R, SN>(Ut, a);
+    const R Tc = col_centre<R, SN>(T, a), cc = col_centre<R, SN>(cp, a);
+    h0 = (cc * Tc) * q_centre<R, SN>(un, ut);
+    R qp, qm;
+    q_tpoints<R, SN>(un, ut, b * col_dt<R, SN>(Un), b * col_dt<R, SN>(Ut), qp, qm);
+    const R dT = b * col_dt<R, SN>(T), dc = b * col_dt<R, SN>(cp);
+    hs = fma((cc - dc) * (Tc - dT), qp, ((cc + dc) * (Tc + dT)) * qm);
 }
 
 template <class R, bool AXI>
 __device__ __forceinline__ FaceFlux<R> face_flux_gen(const Consts<R>& K, const Ring<R>& P, const FaceIdx& x,
                                                      bool normal_x, bool normal_is_r, R inv_r) {
-    const R w0 = R(4.0 / 9.0), w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
+    const R w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
     RecN<R> Un, Ut;
     recn2(&P.uv[0][0], x, Un, Ut);
     if (!normal_x) { const RecN<R> t = Un; Un = Ut; Ut = t; }
-    // f: points at dt_f
-    R fq0, pf_a = R(0), mn_a = R(0), mt_a = R(0), pf_d = R(0), mn_d = R(0), mt_d = R(0);
-    R qn_a = R(0), qn_d = R(0), qt_d = R(0), rho_f, unf0, utf0;
     RecN<R> Rho, Cc;
     recn2(&P.rc[0][0], x, Rho, Cc);
+    // f: points at dt_f; the face column (e_n = 0) shifts by (dt/4)(d_t f_L + d_t f_R)
+    R pf_n, mn_n, mt_n, Snn_q, Snt_q;
+    const R rho_f = Rho.o0;
     {
-        R un[9], ut[9], rr[9];
-        points_dt(Un, K.dtf, un);
-        points_dt(Ut, K.dtf, ut);
-        points_dt(Rho, K.dtf, rr);
-        rho_f = rr[0];
-        unf0 = un[0];
-        utf0 = ut[0];
-        fq0 = rr[0] * (R(-0.5) * (un[0] * un[0] + ut[0] * ut[0]));
-#pragma unroll
-        for (int a = 1; a < 9; ++a) {
-            const int en = e_n(a), et = e_t(a);
-            const R eu = e_dot(a, un[a], ut[a]);
-            const R q = eu + R(1.5) * eu * eu - R(0.5) * (un[a] * un[a] + ut[a] * ut[a]);
-            const R fq = rr[a] * q;
-            if (a < 5) {
-                pf_a += fq;
-                if (en != 0) { mn_a += en > 0 ? fq : -fq; qn_a += q; }
-                if (et != 0) mt_a += et > 0 ? fq : -fq;
-            } else {
-                pf_d += fq;
-                mn_d += en > 0 ? fq : -fq;
-                mt_d += et > 0 ? fq : -fq;
-                qn_d += q;
-                qt_d += en * et > 0 ? q : -q;
-            }
-        }
+        const R a = R(0.5) - K.dtf, b = R(0.5) * K.dtf, h = R(0.5) * b;
+        const ColF<R> L = col_f<R, 1>(Un, Ut, Rho, a, b);
+        const ColF<R> Rs = col_f<R, -1>(Un, Ut, Rho, a, b);
+        const R stn = h * (Un.dtl + Un.dtr), stt = h * (Ut.dtl + Ut.dtr), str = h * (Rho.dtl + Rho.dtr);
+        const R un2 = Un.o0 - stn, un4 = Un.o0 + stn, ut2 = Ut.o0 - stt, ut4 = Ut.o0 + stt;
+        const R q2 = fma(ut2, ut2, fma(R(-0.5) * un2, un2, ut2));
+        const R q4 = fma(ut4, ut4, fma(R(-0.5) * un4, un4, -ut4));
+        const R a4 = (Rho.o0 + str) * q4;
+        const R f24s = fma(Rho.o0 - str, q2, a4), f24d = fma(Rho.o0 - str, q2, -a4);
+        const R ruu0 = rho_f * fma(Un.o0, Un.o0, Ut.o0 * Ut.o0);
+        pf_n = R(-2.0 / 9.0) * ruu0 + w1 * ((L.f0 + Rs.f0) + f24s) + w5 * (L.fs + Rs.fs);
+        mn_n = w1 * (L.f0 - Rs.f0) + w5 * (L.fs - Rs.fs);
+        mt_n = w1 * f24d + w5 * (L.fd + Rs.fd);
+        Snn_q = w1 * (L.q0 + Rs.q0) + w5 * (L.qs + Rs.qs);
+        Snt_q = w5 * (L.qd - Rs.qd);
     }
     // g: points at dt_g
-    R ce_a = R(0), ce_d = R(0), cen_a = R(0), cen_d = R(0), Cface;
+    R ce_a, cen_a, ce_d, cen_d;
     {
-        R un[9], ut[9], CC[9];
-        points_dt(Un, K.dtg, un);
-        points_dt(Ut, K.dtg, ut);
-        points_dt(Cc, K.dtg, CC);
-        Cface = CC[0];
-#pragma unroll
-        for (int a = 1; a < 9; ++a) {
-            const int en = e_n(a);
-            const R ce = CC[a] * e_dot(a, un[a], ut[a]);
-            if (a < 5) { ce_a += ce; if (en != 0) cen_a += en > 0 ? ce : -ce; }
-            else { ce_d += ce; cen_d += en > 0 ? ce : -ce; }
-        }
+        const R a = R(0.5) - K.dtg, b = R(0.5) * K.dtg, h = R(0.5) * b;
+        R c0L, csL, c0R, csR;
+        col_g<R, 1>(Un, Ut, Cc, a, b, c0L, csL);
+        col_g<R, -1>(Un, Ut, Cc, a, b, c0R, csR);
+        const R stt = h * (Ut.dtl + Ut.dtr), stc = h * (Cc.dtl + Cc.dtr);
+        const R c24 = fma(Cc.o0 - stc, Ut.o0 - stt, -((Cc.o0 + stc) * (Ut.o0 + stt)));
+        ce_a = (c0L - c0R) + c24;
+        cen_a = c0L + c0R;
+        ce_d = csL + csR;
+        cen_d = csL - csR;
     }
     // h: points at dt_h (only e_n != 0 points carry C_p T q into the flux)
-    R th_a = R(0), th_d = R(0);
     RecN<R> T, cp;
     recn2(&P.tc[0][0], x, T, cp);
+    R th_a, th_d;
     {
-        R un[9], ut[9], Tp[9], cpp[9];
-        points_dt(Un, K.dth, un);
-        points_dt(Ut, K.dth, ut);
-        points_dt(T, K.dth, Tp);
-        points_dt(cp, K.dth, cpp);
-#pragma unroll
-        for (int a = 1; a < 9; ++a) {
-            const int en = e_n(a);
-            if (en == 0) continue;
-            const R eu = e_dot(a, un[a], ut[a]);
-            const R q = eu + R(1.5) * eu * eu - R(0.5) * (un[a] * un[a] + ut[a] * ut[a]);
-            const R thq = (cpp[a] * Tp[a]) * q;
-            if (a < 5) th_a += en > 0 ? thq : -thq;
-            else th_d += en > 0 ? thq : -thq;
-        }
+        const R a = R(0.5) - K.dth, b = R(0.5) * K.dth;
+        R h0L, hsL, h0R, hsR;
+        col_h<R, 1>(Un, Ut, T, cp, a, b, h0L, hsL);
+        col_h<R, -1>(Un, Ut, T, cp, a, b, h0R, hsR);
+        th_a = h0L - h0R;
+        th_d = hsL - hsR;
     }
     RecN<R> p, mu;
     recn2(&P.pm[0][0], x, p, mu);
     R lamf, muf;
     face_value2(&P.lm[0][0], x, lamf, muf);
+    const Q4<R> fc = ld4(K.facec);   // Q, C_ref / 6, 6 / C_ref, tau_g - 1/2
     const R af = R(0.5) - K.dtf, ag = R(0.5) - K.dtg, ah = R(0.5) - K.dth;
     const R pl = p.l + af * p.gl, pr = p.r - af * p.gr;
     const R ml = mu.l + ag * mu.gl, mr = mu.r - ag * mu.gr;
     const R Tl = T.l + ah * T.gl, Tr = T.r - ah * T.gr;
-    const R pf = R(2.0 / 3.0) * p.o0 + R(1.0 / 6.0) * (pl + pr) + w0 * fq0 + w1 * pf_a + w5 * pf_d;
-    const R mn = R(1.0 / 6.0) * (pl - pr) + w1 * mn_a + w5 * mn_d;
-    const R mt = -(K.dtf * R(1.0 / 12.0)) * (p.dtl + p.dtr) + w1 * mt_a + w5 * mt_d;
-    const R Cf = Cface + K.Qg * (R(0.5) * (ml + mr) - mu.o0) + R(1.0 / 3.0) * ce_a + R(1.0 / 12.0) * ce_d;
-    const R Sg = R(0.5) * K.Qg * (ml - mr) + R(1.0 / 3.0) * cen_a + R(1.0 / 12.0) * cen_d;
-    const R Sh = R(1.0 / 6.0) * K.Cref * (Tl - Tr) + R(1.0 / 3.0) * th_a + R(1.0 / 12.0) * th_d;
+    const R pf = R(2.0 / 3.0) * p.o0 + R(1.0 / 6.0) * (pl + pr) + pf_n;
+    const R mn = R(1.0 / 6.0) * (pl - pr) + mn_n;
+    const R mt = -(K.dtf * R(1.0 / 12.0)) * (p.dtl + p.dtr) + mt_n;
+    const R Cf = Cc.o0 + fc.x * (R(0.5) * (ml + mr) - mu.o0) + R(1.0 / 3.0) * ce_a + R(1.0 / 12.0) * ce_d;
+    const R Sg = R(0.5) * fc.x * (ml - mr) + R(1.0 / 3.0) * cen_a + R(1.0 / 12.0) * cen_d;
+    const R Sh = fc.y * (Tl - Tr) + R(1.0 / 3.0) * th_a + R(1.0 / 12.0) * th_d;
     const R Snn_p = R(1.0 / 6.0) * (pl + pr);
     const R Snt_p = (K.dtf * R(1.0 / 36.0)) * (p.dtr - p.dtl);
-    const R Snn_q = w1 * qn_a + w5 * qn_d;
-    const R Snt_q = w5 * qt_d;
     const R irf = wdiv(R(1), rho_f);
     const R unf = R(3) * mn * irf, utf = R(3) * mt * irf;
     const R th = K.th_coef * lamf * irf;
     const R tf = K.tf_coef * muf * irf;
-    const R tg = K.tau_g - R(0.5);
+    const R tg = fc.w;
     const R cs2 = R(1.0 / 3.0);
     FaceFlux<R> F;
     F.Fh = (R(1) - th) * (cp.o0 * T.o0) * unf + th * Sh;
@@ -523,7 +552,7 @@ __device__ __forceinline__ FaceFlux<R> face_flux_gen(const Consts<R>& K, const R
     F.Fmt = (R(1) - tf) * cs2 * rho_f * unf * utf + tf * (Snt_p + rho_f * Snt_q);
     F.Fc = (R(1) - tg) * Cf * unf + tg * Sg;
     F.un = unf;
-    if (AXI) F.Fmn += -(K.dtf * R(1.0 / 9.0)) * rho_f * (normal_is_r ? unf0 : utf0) * inv_r;
+    if (AXI) F.Fmn += -(K.dtf * R(1.0 / 9.0)) * rho_f * (normal_is_r ? Un.o0 : Ut.o0) * inv_r;
     return F;
 }
 
