@@ -38,11 +38,11 @@ STAGES = 3
 # operations (FFMA counted as 2) and warp instructions issued.  They are the
 # formulation's arithmetic and the kernel's instruction stream, so they change
 # only with the face/cell algebra or the code.
-FP32_FLOPS_PER_CELL_STAGE = {"rz": 944, "xy": 901}
-WARP_INST_PER_CELL_STAGE = {"rz": 44.8, "xy": 42.5}
+FP32_FLOPS_PER_CELL_STAGE = {"rz": 945, "xy": 901}
+WARP_INST_PER_CELL_STAGE = {"rz": 43.7, "xy": 41.7}
 # DRAM bytes per cell per launch of the stage kernel (ncu, average of the 3
 # stages of the same capture, scaled by cells).
-DRAM_BYTES_PER_CELL_LAUNCH = 65.1
+DRAM_BYTES_PER_CELL_LAUNCH = 64.4
 # FP64 operations per cell per stage of the FP64 stage kernel (DFMA counted as
 # 2), from the ncu counters of one capture of each geometry.
 FP64_FLOPS_PER_CELL_STAGE = {"rz": 1035, "xy": 958}

@@ -49,6 +49,15 @@ def test_fp64_streaming_steps_match_oracle(name, make, nsteps):
         assert abs(dg[k] - dr[k]) <= 1e-10 * max(abs(dr[k]), 1.0), k
 
 
+def test_fp64_benchmark_steps_on_a_batch_domain():
+    """The steps the benchmark's general-streaming leg times, (0.3, 0.4, 0.3),
+    on the smallest droplet of its (r, z) batch."""
+    cases = wl.static_droplet_batch(64, seed=4, axisymmetric=True)
+    case = steps(min(cases, key=lambda c: c.cells), 0.3, 0.4, 0.3)
+    gpu, ref = run_pair(case, 60)
+    assert_fields_close(gpu.fields(), ref.fields(), 1e-10, what=case.name, floor=1e-8)
+
+
 @pytest.mark.parametrize("nx,ny,per", [(33, 5, False), (37, 9, True)])
 def test_fp64_streaming_steps_ragged(nx, ny, per):
     case = steps(ragged_case(nx, ny, per), 0.3, 0.45, 0.4)
