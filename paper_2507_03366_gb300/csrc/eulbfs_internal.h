@@ -58,9 +58,8 @@ struct Consts {
     // face {Q, C_ref / 6, 6 / C_ref, tau_g - 1/2}; cell {kv, g_x, g_y, 1 / dt}
     // and {2 beta, kappa, dt, dt_f}
     Q4<R> mcp, mrho, mlam, mmu, enth, facec, cellc, cellc2;
-    R rho[3], mu[3], lam[3], cp[3];
-    R L, Ts, Tl, beta, kappa, Qg, tau_g, Cref, kv, gx, gy, dt;
-    R six_over_Cref, inv_dt;   // 6 / C_ref = 1 / (C_ref cs^2 dt_s), 1 / dt
+    R cp[3];                   // solid, liquid, gas (the forward closure of the initial state)
+    R L, Ts, Tl;
     R dth, dtf, dtg;           // streaming steps of h, f, g
     R th_coef, tf_coef;        // 3 / (C_ref dt_h), 3 / dt_f: tau - 1/2 = coef x lambda (or mu) / rho
     R Tw[4], wet[4], cos_adv[4], cos_rec[4];
@@ -99,20 +98,14 @@ __host__ __device__ inline void fill_consts(const DomainDesc& d, Consts<R>& K) {
     K.facec = make_q4<R>(d.Qg, d.Cref / 6.0, 6.0 / d.Cref, d.tau_g - 0.5);
     K.cellc = make_q4<R>(d.kv, d.gx, d.gy, 1.0 / d.dt);
     K.cellc2 = make_q4<R>(2.0 * d.beta, d.kappa, d.dt, d.dts[1]);
-    for (int k = 0; k < 3; ++k) {
-        K.rho[k] = (R)d.rho[k]; K.mu[k] = (R)d.mu[k]; K.lam[k] = (R)d.lam[k]; K.cp[k] = (R)d.cp[k];
-    }
-    K.L = (R)d.L; K.Ts = (R)d.Ts; K.Tl = (R)d.Tl; K.beta = (R)d.beta; K.kappa = (R)d.kappa;
-    K.Qg = (R)d.Qg; K.tau_g = (R)d.tau_g; K.Cref = (R)d.Cref; K.kv = (R)d.kv;
-    K.gx = (R)d.gx; K.gy = (R)d.gy; K.dt = (R)d.dt;
-    K.six_over_Cref = (R)(6.0 / d.Cref);
+    for (int k = 0; k < 3; ++k) K.cp[k] = (R)d.cp[k];
+    K.L = (R)d.L; K.Ts = (R)d.Ts; K.Tl = (R)d.Tl;
     K.four_over_xi = (R)d.four_over_xi;
     K.dth = (R)d.dts[0]; K.dtf = (R)d.dts[1]; K.dtg = (R)d.dts[2];
     K.th_coef = (R)(3.0 / (d.Cref * d.dts[0]));
     K.tf_coef = (R)(3.0 / d.dts[1]);
     K.gen = (d.dts[0] != 0.5 || d.dts[1] != 0.5 || d.dts[2] != 0.5) ? 1 : 0;
     K.pad2_ = 0;
-    K.inv_dt = (R)(1.0 / d.dt);
     for (int k = 0; k < 4; ++k) {
         K.Tw[k] = (R)d.Tw[k]; K.wet[k] = (R)d.wet[k];
         K.cos_adv[k] = (R)d.cos_adv[k]; K.cos_rec[k] = (R)d.cos_rec[k];
