@@ -361,9 +361,11 @@ __device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const Ring<
 // its value is f' -/+ (dt/2) d_t f with f' = f + a g_n (g_n the central
 // n-slope of that cell); the face points move by -/+ (dt/4)(d_t f_L + d_t f_R).
 // The closed forms of the linear parts keep their shape with f' for f and
-// dt/12, dt/36 for the t-moments; the per-point sums run once per
-// distribution on its own points.  Used only when some step differs from
-// 1/2; face_flux above is this with a = 0, dt = 1/2.
+// dt/12, dt/36 for the t-moments; the nonlinear sums run once per
+// distribution on its own points, by face columns as in face_flux (the
+// centre of a side column at f', its t-points at f' -/+ (dt/2) d_t f).  Used
+// only when some step differs from 1/2; face_flux above is this with a = 0,
+// dt = 1/2.
 // ---------------------------------------------------------------------------
 template <class R>
 struct RecN { R l, r, gl, gr, o0, dtl, dtr; };
