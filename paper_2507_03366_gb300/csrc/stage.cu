@@ -562,7 +562,7 @@ __device__ __forceinline__ FaceFlux<R> face_flux_gen(const Consts<R>& K, const R
 // l+2 and l+3 (cells x0+l-1 and x0+l), at x = x0 + l.  In an axisymmetric
 // domain the stored fluxes are multiplied by the face area r_f = x0 + l.
 template <class R, bool AXI, bool GEN>
-__device__ __forceinline__ void x_face(Smem<R>& S, int x0, int r, int row_in_chunk, int lane) {
+__device__ __forceinline__ void x_face(Smem<R>& S, int x0, int r, int row_in_chunk, int lane, R inv_rf) {
     FaceIdx x;
     const int cL = lane + 2;
     x.L = slot(r) * RW + cL;
@@ -573,9 +573,7 @@ __device__ __forceinline__ void x_face(Smem<R>& S, int x0, int r, int row_in_chu
     x.Lm = slot(r - 1) * RW + cL;
     x.Rp = x.Lp + 1;
     x.Rm = x.Lm + 1;
-    const int gf = x0 + lane;
-    const R rf = AXI ? (R)gf : R(1);
-    const R inv_rf = (AXI && gf > 0) ? wdiv(R(1), rf) : R(0);
+    const R rf = AXI ? (R)(x0 + lane) : R(1);
     FaceFlux<R> F = GEN ? face_flux_gen<R, AXI>(S.K, S.P, x, true, true, inv_rf)
                         : face_flux<R, AXI>(S.K, S.P, x, true, true, inv_rf);
     if (AXI) {
@@ -589,7 +587,7 @@ __device__ __forceinline__ void x_face(Smem<R>& S, int x0, int r, int row_in_chu
 // Step 3, y-faces of face row r (between rows r-1 and r), lane l < 31 at
 // column l+3 (cell x0 + l, radius x0 + l + 1/2 in an axisymmetric domain).
 template <class R, bool AXI, bool GEN>
-__device__ __forceinline__ void y_face(Smem<R>& S, int x0, int r, int lane) {
+__device__ __forceinline__ void y_face(Smem<R>& S, int r, int lane, R inv_r) {
     FaceIdx x;
     const int c = lane + kHalo;
     x.L = slot(r - 1) * RW + c;
@@ -600,7 +598,6 @@ __device__ __forceinline__ void y_face(Smem<R>& S, int x0, int r, int lane) {
     x.Lm = x.L - 1;
     x.Rp = x.R + 1;
     x.Rm = x.R - 1;
-    const R inv_r = AXI ? wdiv(R(1), (R)(x0 + lane) + R(0.5)) : R(0);
     const FaceFlux<R> F = GEN ? face_flux_gen<R, AXI>(S.K, S.P, x, false, false, inv_r)
                               : face_flux<R, AXI>(S.K, S.P, x, false, false, inv_r);
     const int s = slot(r);
@@ -612,7 +609,7 @@ __device__ __forceinline__ void y_face(Smem<R>& S, int x0, int r, int lane) {
 // Step 4 for the cell (r, x0 + lane).
 template <class R, bool AXI>
 __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r, int row_in_chunk, int lane,
-                                            int* flag) {
+                                            R irc, int* flag) {
     const Consts<R>& K = S.K;
     const int gx = x0 + lane;
     const long long c = (long long)r * K.nx + gx;
@@ -620,8 +617,7 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
     const int qn = slot(r + 1) * RW + lane + kHalo, qs = slot(r - 1) * RW + lane + kHalo;
     const int sr = slot(r), sn = slot(r + 1);
     // Eq. 52; axisymmetric: the x-face fluxes carry their areas r_f, divided
-    // here by the cell volume r_i = gx + 1/2 (per radian)
-    const R irc = AXI ? wdiv(R(1), (R)gx + R(0.5)) : R(1);
+    // here by the cell volume r_i = gx + 1/2 (per radian); irc = 1 / r_i
     R Rk[5], divu;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -721,13 +717,18 @@ template <class R, bool AXI, bool GEN>
 __device__ __forceinline__ void sweep_item(Smem<R>& S, const StageLaunch& a, int x0, int y0, int y1) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const R* in = reinterpret_cast<const R*>(S.K.st[a.stage]);
+    // a lane keeps its column through the item: in an axisymmetric domain
+    // 1 / r of its cell centre (y-faces, cell volume) and of its x-face
+    // (0 on the axis, where the face area is zero)
+    const R ir_c = AXI ? wdiv(R(1), (R)(x0 + lane) + R(0.5)) : R(1);
+    const R ir_f = (AXI && x0 + lane > 0) ? wdiv(R(1), (R)(x0 + lane)) : R(0);
 
     // prologue: rows y0-3 .. y0+2, mu_c of rows y0-2 .. y0+1, y-face row y0
     load_rows(S, in, x0, y0 - kHalo, 2 * kHalo);
     __syncthreads();
     muc_rows<R, AXI>(S, x0, y0 - 2, 4);
     __syncthreads();
-    if (warp == 0 && lane < kStripX) y_face<R, AXI, GEN>(S, x0, y0, lane);
+    if (warp == 0 && lane < kStripX) y_face<R, AXI, GEN>(S, y0, lane, AXI ? ir_c : R(0));
     // (the first chunk writes other ring rows: no barrier needed here)
 
     for (int j0 = y0; j0 < y1; j0 += kChunk) {
@@ -738,13 +739,13 @@ __device__ __forceinline__ void sweep_item(Smem<R>& S, const StageLaunch& a, int
         // one face at a time per thread (x then y) keeps register use low
 #pragma unroll 1
         for (int k = 0; k < 2; ++k) {
-            if (k == 0) x_face<R, AXI, GEN>(S, x0, j0 + warp, warp, lane);
-            else if (lane < kStripX) y_face<R, AXI, GEN>(S, x0, j0 + 1 + warp, lane);
+            if (k == 0) x_face<R, AXI, GEN>(S, x0, j0 + warp, warp, lane, ir_f);
+            else if (lane < kStripX) y_face<R, AXI, GEN>(S, j0 + 1 + warp, lane, AXI ? ir_c : R(0));
         }
         __syncthreads();
         const int r = j0 + warp;
         if (r < y1 && lane < kStripX && x0 + lane < S.K.nx)
-            cell_update<R, AXI>(S, a.stage, x0, r, warp, lane, a.flag);
+            cell_update<R, AXI>(S, a.stage, x0, r, warp, lane, ir_c, a.flag);
         __syncthreads();
     }
 }
