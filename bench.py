@@ -38,8 +38,8 @@ STAGES = 3
 # operations (FFMA counted as 2) and warp instructions issued.  They are the
 # formulation's arithmetic and the kernel's instruction stream, so they change
 # only with the face/cell algebra or the code.
-FP32_FLOPS_PER_CELL_STAGE = {"rz": 945, "xy": 901}
-WARP_INST_PER_CELL_STAGE = {"rz": 43.7, "xy": 41.7}
+FP32_FLOPS_PER_CELL_STAGE = {"rz": 939, "xy": 901}
+WARP_INST_PER_CELL_STAGE = {"rz": 43.1, "xy": 41.7}
 # DRAM bytes per cell per launch of the stage kernel (ncu, average of the 3
 # stages of the same capture, scaled by cells).
 DRAM_BYTES_PER_CELL_LAUNCH = 64.4
