@@ -194,6 +194,14 @@ def cpu_baseline(cases, seconds: float) -> dict:
 METRIC = "GCUPS coupled EULBFS step, FP32 batched vs FP64 plain; p50/p99 solve latency"
 
 
+def binding_roof(bytes_per_launch: float, flops_per_launch: float, hbm_gbs: float, fp32_tflops: float) -> str:
+    """The roof that bounds a launch: the one whose minimum time (bytes over
+    bandwidth, or flops over the FP32 rate) is the longer; "hbm" on a tie."""
+    t_mem = bytes_per_launch / (hbm_gbs * 1e9)
+    t_alu = flops_per_launch / (fp32_tflops * 1e12)
+    return "hbm" if t_mem >= t_alu else "alu"
+
+
 def workload_config(cases, world: int, args) -> dict:
     cells = sum(c.cells for c in cases)
     geo = "axisymmetric (r, z)" if cases and cases[0].axisymmetric else "planar 2-D"
@@ -309,7 +317,7 @@ def main():
            "flops_per_launch": flops}
     mem = {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
            "peak_source": "measured" if peaks else "fallback", "algorithmic_bytes_per_launch": alg_bytes}
-    hbm_bound = alg_bytes / (hbm * 1e9) >= flops / (fp32_peak * 1e12)
+    hbm_bound = binding_roof(alg_bytes, flops, hbm, fp32_peak) == "hbm"
     top, other = (mem, alu) if hbm_bound else (alu, mem)
     roofline = {"bound": "hbm" if hbm_bound else "alu", **top, "traffic": DRAM_BYTES_PER_CELL_LAUNCH * cells,
                 "kernel": "eulbfs::stage_kernel<float>", "avg_launch_ms": per_launch_ms,
