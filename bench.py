@@ -70,7 +70,7 @@ def parse():
                     help="steps of the general-streaming-step leg (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--serve", type=int, default=200, help="requests in the serving leg (0: skip)")
+    ap.add_argument("--serve", type=int, default=500, help="requests in the serving leg (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=4.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--geometry", default="rz", choices=["rz", "xy"],
