@@ -84,6 +84,16 @@ typedef struct {
     double tau_g;          /* phase-field relaxation parameter, > 0.5 */
     double gx, gy;         /* gravitational acceleration, G = rho g (Eq. 51) */
     int zero_solid_velocity; /* 1: momentum of the solid part projected to zero */
+    /* 0 (default): Eq. 5-7 gated by the phase field, C~ = clamp(C, 0, 1):
+     * gamma = C~ [F_s gamma_s + F_l gamma_l] + (1 - C~) gamma_g, heat
+     * capacities of both branches of Eq. 6 mixed the same way, and C~ F_s as
+     * the solid fraction of the volume-change sources (Eq. 26, 27) and of the
+     * solid projection.  Without the gate, Eq. 7 with F_s from Eq. 5 turns gas
+     * colder than T_s into solid.  1: Eq. 5-7 exactly as printed:
+     * gamma = F_s gamma_s + (1 - F_s) C~ gamma_l + (1 - F_s)(1 - C~) gamma_g,
+     * H_s = C_p,s T_s, H_l = C_p,l T_l + L, and F_s itself in those sources
+     * (C~ still bounds the mixture, so an overshoot of C cannot make rho <= 0). */
+    int literal_eq7;
 } eulbfs_props;
 
 /* Tw: wall temperature (DIRICHLET_T).  theta_deg: contact angle (WETTING),
@@ -149,8 +159,14 @@ typedef struct {
 
 typedef struct eulbfs_solver eulbfs_solver;
 
-/* Create a solver holding one domain.  stream is a cudaStream_t the solver
- * enqueues all its work on, or NULL for a stream the solver owns.
+/* Create a solver holding one domain: the problem as Sec. 3 states each
+ * case -- a uniform grid (Sec. 3.1-3.5), the three phases' properties
+ * (Tables 1 and 3: rho, mu, lambda, C_p; L, T_s, T_l, sigma, xi, M_c), the
+ * boundary conditions per field and side (Sec. 3.1-3.5), the time steps
+ * (Sec. 2.4 after Eq. 58, Sec. 2.5 step (1)) and the initial fields (e.g.
+ * Eq. 61-62), from which H = C_p T + L F_l (Eq. 5-7) is formed on the device.
+ * stream is a cudaStream_t the solver enqueues all its work on, or NULL for a
+ * stream the solver owns.
  * Errors: EINVAL (bad sizes or parameters: tau <= 0.5, rho/lambda/cp <= 0,
  * inconsistent periodic sides, dt <= 0), ECUDA, ENOMEM. */
 int eulbfs_create(const eulbfs_grid* grid, const eulbfs_props* props, const eulbfs_bc* bc,
@@ -158,7 +174,9 @@ int eulbfs_create(const eulbfs_grid* grid, const eulbfs_props* props, const eulb
                   void* stream, eulbfs_solver** out);
 
 /* Create a solver holding n >= 0 domains of any sizes and parameters that
- * advance together: every stage of every domain runs in one launch over a
+ * advance together (no counterpart in the paper, which runs one domain at a
+ * time; each domain is the problem eulbfs_create describes): every stage of
+ * every domain runs in one launch over a
  * work list of strip segments (many uneven domains).  n = 0 creates an empty
  * solver that eulbfs_add_domain fills (a serving loop). */
 int eulbfs_batch_create(int n, const eulbfs_domain* domains, int precision, void* stream,
@@ -185,8 +203,12 @@ int eulbfs_num_slots(const eulbfs_solver* s);
 /* Steps completed and steps left (-1 = unlimited) of a domain. */
 int eulbfs_domain_progress(const eulbfs_solver* s, int slot, long long* done, long long* left);
 
-/* Advance every active domain by n >= 0 time steps (a domain with a step
- * limit stops at it).  Work is enqueued on the solver's stream and the call
+/* Advance every active domain by n >= 0 time steps of Sec. 2.5, steps
+ * (1)-(7): per Runge-Kutta stage of Eq. 58, the face fluxes of Eq. 53 from
+ * the reconstruction (Eq. 54), the surrounding and face equilibria (Eq. 9,
+ * 29, 33, 42, 56) and the star distributions (Eq. 13/16, 35/37, 44/46), the
+ * sources of Eq. 51 and the residual of Eq. 52; then Eq. 5-7 on the new state
+ * (a domain with a step limit stops at it).  Work is enqueued on the solver's stream and the call
  * returns without waiting; launch errors are reported, a non-finite state is
  * reported by eulbfs_sync / eulbfs_diagnostics / eulbfs_fields. */
 int eulbfs_step(eulbfs_solver* s, long long n);
@@ -195,8 +217,20 @@ int eulbfs_step(eulbfs_solver* s, long long n);
  * domain produced a NaN or Inf since the solver was created. */
 int eulbfs_sync(eulbfs_solver* s);
 
+/* Slots of the live domains whose own state became NaN or Inf (their
+ * per-domain flag; other domains are unaffected and keep stepping).
+ * Synchronises the solver's stream.  Up to `cap` slot indices are written to
+ * the caller-owned `slots`; *count receives the number of such domains (it
+ * may exceed cap).  A serving loop calls it after each batch of steps to
+ * retire a diverged case at once instead of at its step limit.
+ * Errors: EINVAL (null solver or count, cap < 0, slots NULL with cap > 0),
+ * ENOMEM, ECUDA. */
+int eulbfs_nonfinite_domains(eulbfs_solver* s, int* slots, int cap, int* count);
+
 /* Copy primitive fields of domain `slot` to caller-owned host arrays
- * (synchronises the solver's stream).  Returns ENONFINITE (after copying) if
+ * (synchronises the solver's stream): H and C from the state W (Eq. 49), T
+ * and F_l by Eq. 5-6, u = W_3 / (rho cs^2), v = W_4 / (rho cs^2) with rho from
+ * Eq. 7, and p.  Returns ENONFINITE (after copying) if
  * this domain produced a NaN or Inf; other domains do not affect it. */
 int eulbfs_fields(eulbfs_solver* s, int slot, const eulbfs_fields_out* out);
 
@@ -222,7 +256,12 @@ int eulbfs_save(eulbfs_solver* s, int slot, void* buf, unsigned long long bytes,
 int eulbfs_load(eulbfs_solver* s, int slot, const void* buf, unsigned long long bytes, long long step);
 
 /* FP64 diagnostics of domain `slot` (synchronises the solver's stream);
- * ENONFINITE (with d filled) if this domain's state is not finite. */
+ * ENONFINITE (with d filled) if this domain's state is not finite.  They are
+ * the quantities Sec. 3 measures: the front position of the Neumann problem
+ * (Sec. 3.1, Eq. 59-60) and the interface position of the expansion law
+ * H_f = (rho_l / rho_s) H_0 (Sec. 3.2) as flat-layer heights of the solid
+ * and condensed volumes, those volumes themselves (Table 2, Table 5), the
+ * total mass, enthalpy and largest speed. */
 int eulbfs_diagnostics(eulbfs_solver* s, int slot, eulbfs_diag* d);
 
 /* Number of kernels the solver launches per time step of the current batch. */
@@ -262,8 +301,9 @@ int eulbfs_set_tile(eulbfs_solver* s, int rows);
  * partials it uses, so nothing needs clearing, but calls that overlap on the
  * GPU (different streams or host threads) race on it and must be serialised.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. */
+ * (cudaGetSymbolAddress) with that device current, and looks it up again
+ * when the device's context has changed (after cudaDeviceReset); make that
+ * first call before any stream capture. */
 #define EULBFS_NOALLOC_MAX_CELLS 2097152
 int eulbfs_diagnostics_noalloc(int precision, const void* state, int nx, int ny,
                                const eulbfs_props* props, double* out, void* stream);

@@ -49,7 +49,7 @@ class Props(ct.Structure):
     _fields_ = [("s", Phase), ("l", Phase), ("g", Phase), ("L", ct.c_double), ("Ts", ct.c_double),
                 ("Tl", ct.c_double), ("sigma", ct.c_double), ("xi", ct.c_double), ("Mc", ct.c_double),
                 ("tau_g", ct.c_double), ("gx", ct.c_double), ("gy", ct.c_double),
-                ("zero_solid_velocity", ct.c_int)]
+                ("zero_solid_velocity", ct.c_int), ("literal_eq7", ct.c_int)]
 
 
 class Side(ct.Structure):
@@ -122,7 +122,7 @@ def _ptr(a: np.ndarray):
 def props_struct(p) -> Props:
     ph = lambda q: Phase(q.rho, q.mu, q.lam, q.cp)  # noqa: E731
     return Props(ph(p.s), ph(p.l), ph(p.g), p.L, p.Ts, p.Tl, p.sigma, p.xi, p.Mc, p.tau_g, p.gx, p.gy,
-                 int(p.zero_solid_velocity))
+                 int(p.zero_solid_velocity), int(getattr(p, "literal_eq7", 0)))
 
 
 def bc_struct(b) -> BC:

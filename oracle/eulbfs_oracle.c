@@ -76,12 +76,28 @@ static int PI(const or_solver* s, int i, int j) { return (j + NG) * s->px + (i +
  * H_s and H_l of Eq. 5-6 are the enthalpies of the cell fully solid at T_s
  * and fully liquid at T_l.  Reading R2: the solid branch uses the
  * solid-state mixture Cp, the liquid branch the liquid-state mixture Cp. */
-void or_invert_enthalpy(const or_props* P, double H, double C, double* T, double* Fl) {
+/* The heat capacities of the solid and liquid branches of Eq. 6 and the
+ * enthalpies H_s, H_l of Eq. 5-6.  Reading R1: gated mixtures.  Eq. 7 as
+ * printed (literal_eq7): H_s = C_p,s T_s and H_l = C_p,l T_l + L with the pure
+ * phases' heat capacities; the solid branch's C_p is Eq. 7 at F_s = 1, i.e.
+ * C_p,s, the liquid branch's is Eq. 7 at F_s = 0, C~ C_p,l + (1 - C~) C_p,g. */
+static void branch_constants(const or_props* P, double C, double* cps, double* cpl, double* Hs, double* Hl) {
     const double Ct = clamp01(C);
-    const double cps = Ct * P->s.cp + (1.0 - Ct) * P->g.cp;
-    const double cpl = Ct * P->l.cp + (1.0 - Ct) * P->g.cp;
-    const double Hs = cps * P->Ts;
-    const double Hl = cpl * P->Tl + P->L;
+    *cpl = Ct * P->l.cp + (1.0 - Ct) * P->g.cp;
+    if (P->literal_eq7) {
+        *cps = P->s.cp;
+        *Hs = P->s.cp * P->Ts;
+        *Hl = P->l.cp * P->Tl + P->L;
+    } else {
+        *cps = Ct * P->s.cp + (1.0 - Ct) * P->g.cp;
+        *Hs = *cps * P->Ts;
+        *Hl = *cpl * P->Tl + P->L;
+    }
+}
+
+void or_invert_enthalpy(const or_props* P, double H, double C, double* T, double* Fl) {
+    double cps, cpl, Hs, Hl;
+    branch_constants(P, C, &cps, &cpl, &Hs, &Hl);
     if (H < Hs) {                 /* Eq. 5-6, first branch */
         *Fl = 0.0;
         *T = H / cps;
@@ -99,11 +115,8 @@ void or_invert_enthalpy(const or_props* P, double H, double C, double* T, double
 
 /* Inverse of Eq. 5-6 used only to build the initial H from (T, F_l, C). */
 double or_enthalpy_of(const or_props* P, double T, double Fl, double C) {
-    const double Ct = clamp01(C);
-    const double cps = Ct * P->s.cp + (1.0 - Ct) * P->g.cp;
-    const double cpl = Ct * P->l.cp + (1.0 - Ct) * P->g.cp;
-    const double Hs = cps * P->Ts;
-    const double Hl = cpl * P->Tl + P->L;
+    double cps, cpl, Hs, Hl;
+    branch_constants(P, C, &cps, &cpl, &Hs, &Hl);
     if (T < P->Ts) return cps * T;
     if (T > P->Tl) return Hl + cpl * (T - P->Tl);
     double f = (P->Tl > P->Ts) ? (T - P->Ts) / (P->Tl - P->Ts) : Fl;
@@ -112,7 +125,8 @@ double or_enthalpy_of(const or_props* P, double T, double Fl, double C) {
     return Hs + f * (Hl - Hs);
 }
 
-/* Eq. 7 with reading R1: gamma = C~[F_s gamma_s + F_l gamma_l] + (1 - C~) gamma_g. */
+/* Eq. 7 with reading R1: gamma = C~[F_s gamma_s + F_l gamma_l] + (1 - C~) gamma_g;
+ * as printed (literal_eq7): F_s gamma_s + (1 - F_s) C~ gamma_l + (1 - F_s)(1 - C~) gamma_g. */
 double or_mix(const or_props* P, double C, double Fl, int which) {
     const double Ct = clamp01(C);
     const double Fs = 1.0 - Fl;
@@ -123,8 +137,13 @@ double or_mix(const or_props* P, double C, double Fl, int which) {
         case 2: gs = P->s.lambda; gl = P->l.lambda; gg = P->g.lambda; break;
         default: gs = P->s.cp; gl = P->l.cp; gg = P->g.cp; break;
     }
+    if (P->literal_eq7) return Fs * gs + (1.0 - Fs) * Ct * gl + (1.0 - Fs) * (1.0 - Ct) * gg;
     return Ct * (Fs * gs + Fl * gl) + (1.0 - Ct) * gg;
 }
+
+/* The factor on F_s in the volume-change sources and the solid projection:
+ * C~ under reading R1, 1 with Eq. 7 as printed. */
+static double solid_gate(const or_props* P, double C) { return P->literal_eq7 ? 1.0 : clamp01(C); }
 
 /* ------------------------------------------------------------------ */
 /* Equilibria.                                                          */
@@ -491,7 +510,7 @@ static void residual(or_solver* s, double* const W[5], double* const R[5]) {
             const double T = s->prim[P_T][q], Fl = s->prim[P_FL][q], Cp = s->prim[P_CP][q];
             const double rho = s->prim[P_RHO][q], u = s->prim[P_U][q], v = s->prim[P_V][q];
             const double C = s->prim[P_C][q];
-            const double D = clamp01(C) * s->dFs[c];   /* solid-volume rate, R1 + R14 */
+            const double D = solid_gate(&s->P, C) * s->dFs[c];   /* solid-volume rate, R1 + R14 */
             const double Fsx = -Fl * C * s->grx[P_MUC][q];   /* F_surf, R13 */
             const double Fsy = -Fl * C * s->gry[P_MUC][q];
             const double Fix = -rho * u * D, Fiy = -rho * v * D;   /* F_IBM (Eq. 27) */
@@ -521,7 +540,7 @@ static void project_solid(or_solver* s) {
     for (int c = 0; c < n; ++c) {
         double T, Fl;
         or_invert_enthalpy(&s->P, s->W[0][c], s->W[4][c], &T, &Fl);
-        const double keep = 1.0 - clamp01(s->W[4][c]) * (1.0 - Fl);
+        const double keep = 1.0 - solid_gate(&s->P, s->W[4][c]) * (1.0 - Fl);
         s->W[2][c] *= keep;
         s->W[3][c] *= keep;
     }

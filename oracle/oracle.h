@@ -43,6 +43,11 @@ typedef struct {
     double tau_g;       /* phase-field relaxation parameter (Sec. 2.3.2) */
     double gx, gy;      /* gravitational acceleration; G = rho*g (Eq. 51) */
     int zero_solid_velocity; /* reading R15: project momentum to zero in solid */
+    /* 0: reading R1 (properties and the volume-change sources gated by
+     * C~ = clamp(C, 0, 1), uniform latent heat).  1: Eq. 5-7 as printed:
+     * F_s = 1 - F_l of every cell (gas included) enters Eq. 7 and the sources,
+     * H_s = C_p,s T_s and H_l = C_p,l T_l + L (C~ still bounds the mixture). */
+    int literal_eq7;
 } or_props;
 
 enum {

@@ -117,6 +117,7 @@ DomainDesc make_desc(const eulbfs_grid& g, const eulbfs_props& P, const eulbfs_b
         d.cos_rec[k] = std::cos(sides[k]->theta_rec_deg * M_PI / 180.0);
     }
     d.zero_solid_velocity = P.zero_solid_velocity ? 1 : 0;
+    d.literal_eq7 = P.literal_eq7 ? 1 : 0;
     d.axi = N.axisymmetric ? 1 : 0;
     const eulbfs_phase* ph[3] = {&P.s, &P.l, &P.g};
     for (int k = 0; k < 3; ++k) {
@@ -171,6 +172,8 @@ struct eulbfs_solver {
     int grid = 1;
     int* d_flag = nullptr;
     int* h_flag = nullptr;
+    int* h_flags = nullptr;        // pinned, one per slot: per-domain non-finite flags
+    int h_flags_cap = 0;
     double* d_partial = nullptr;
     int partial_cap = 0;
     double* d_diag = nullptr;
@@ -597,6 +600,32 @@ int eulbfs_sync(eulbfs_solver* s) {
     return EULBFS_OK;
 }
 
+int eulbfs_nonfinite_domains(eulbfs_solver* s, int* slots, int cap, int* count) {
+    if (!s || !count || cap < 0 || (cap > 0 && !slots)) return fail(EULBFS_EINVAL, "bad arguments");
+    const int nd = (int)s->doms.size();
+    if (nd > s->h_flags_cap) {
+        if (s->h_flags) cudaFreeHost(s->h_flags);
+        s->h_flags = nullptr;
+        s->h_flags_cap = 0;
+        const int want = std::max(nd, 2 * s->h_flags_cap + 16);
+        CK(cudaMallocHost(&s->h_flags, sizeof(int) * want), "flag staging");
+        s->h_flags_cap = want;
+    }
+    for (int k = 0; k < nd; ++k)
+        if (s->doms[k].alive)
+            CK(cudaMemcpyAsync(s->h_flags + k, s->doms[k].desc.flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream),
+               "flag copy");
+    CK(cudaStreamSynchronize(s->stream), "stream sync");
+    int n = 0;
+    for (int k = 0; k < nd; ++k)
+        if (s->doms[k].alive && (s->h_flags[k] & 1)) {
+            if (n < cap) slots[n] = k;
+            ++n;
+        }
+    *count = n;
+    return EULBFS_OK;
+}
+
 int eulbfs_fields(eulbfs_solver* s, int slot, const eulbfs_fields_out* out) {
     int rc = check_slot(s, slot);
     if (rc) return rc;
@@ -755,6 +784,7 @@ void eulbfs_destroy(eulbfs_solver* s) {
     if (s->d_items) cudaFree(s->d_items);
     if (s->d_flag) cudaFree(s->d_flag);
     if (s->h_flag) cudaFreeHost(s->h_flag);
+    if (s->h_flags) cudaFreeHost(s->h_flags);
     if (s->d_partial) cudaFree(s->d_partial);
     if (s->d_diag) cudaFree(s->d_diag);
     if (s->h_diag) cudaFreeHost(s->h_diag);

@@ -21,6 +21,7 @@ struct DomainDesc {
     int bc_t[4], bc_f[4], bc_c[4];  // thermal, flow, phase kind per side
     int zero_solid_velocity;
     int axi;                 // 1: axisymmetric (r, z), x = r with the axis at x = 0
+    int literal_eq7;         // 1: Eq. 5-7 as printed instead of reading R1
     double Tw[4];            // wall temperature per side (Dirichlet)
     double wet[4];           // 4 cos(theta) / xi per side (wetting)
     double cos_adv[4], cos_rec[4];   // hysteresis window per side (WETTING_HYST)
@@ -66,7 +67,7 @@ struct Consts {
     R four_over_xi;
     int nx, ny, per_x, per_y, zsv, axi;
     int gen;                   // 1: some streaming step differs from 0.5 (general face path)
-    int pad2_;
+    int lit;                   // 1: Eq. 5-7 as printed instead of reading R1
     int bc_t[4], bc_f[4], bc_c[4];
     long long plane;
     void* st[3];
@@ -105,7 +106,7 @@ __host__ __device__ inline void fill_consts(const DomainDesc& d, Consts<R>& K) {
     K.th_coef = (R)(3.0 / (d.Cref * d.dts[0]));
     K.tf_coef = (R)(3.0 / d.dts[1]);
     K.gen = (d.dts[0] != 0.5 || d.dts[1] != 0.5 || d.dts[2] != 0.5) ? 1 : 0;
-    K.pad2_ = 0;
+    K.lit = d.literal_eq7;
     for (int k = 0; k < 4; ++k) {
         K.Tw[k] = (R)d.Tw[k]; K.wet[k] = (R)d.wet[k];
         K.cos_adv[k] = (R)d.cos_adv[k]; K.cos_rec[k] = (R)d.cos_rec[k];

@@ -5,6 +5,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cuda.h>
+
 #include <mutex>
 
 #include "device_common.cuh"
@@ -18,10 +20,10 @@ namespace eulbfs {
 // Inverse of Eq. 5-6 for the initial state (same rule as the oracle).
 __device__ double enthalpy_of(const Consts<double>& K, double T, double Fl, double C) {
     const double Ct = clamp01(C);
-    const double cps = Ct * K.cp[0] + (1.0 - Ct) * K.cp[2];
     const double cpl = Ct * K.cp[1] + (1.0 - Ct) * K.cp[2];
+    const double cps = K.lit ? K.cp[0] : Ct * K.cp[0] + (1.0 - Ct) * K.cp[2];
     const double Hs = cps * K.Ts;
-    const double HL = cpl * K.Tl + K.L;
+    const double HL = (K.lit ? K.cp[1] : cpl) * K.Tl + K.L;
     if (T < K.Ts) return cps * T;
     if (T > K.Tl) return HL + cpl * (T - K.Tl);
     const double f = (K.Tl > K.Ts) ? (T - K.Ts) / (K.Tl - K.Ts) : Fl;
@@ -45,7 +47,7 @@ __global__ void init_kernel(const DomainDesc* dd, const double* T, const double*
         const double H = enthalpy_of(Kd, T[c], Fl ? Fl[c] : 1.0, Cc);
         double Td, Fld;
         invert_enthalpy(Kd, H, 0.0, clamp01(Cc), Td, Fld);
-        const double rho = mix(clamp01(Cc), Fld, Kd.mrho);
+        const double rho = mix(clamp01(Cc), Fld, Kd.mrho, Kd.lit);
         SV<R> s;
         if (sizeof(R) == 8) { s.Hh = (R)H; s.Hl = 0; s.Ch = (R)Cc; s.Cl = 0; }
         else { put_pair(s.Hh, s.Hl, H); put_pair(s.Ch, s.Cl, Cc); }
@@ -73,7 +75,7 @@ __global__ void fields_kernel(const DomainDesc* dd, long long n, double* H, doub
         const double Hd = pair_value(w.Hh, w.Hl), Cd = pair_value(w.Ch, w.Cl);
         double Td, Fld;
         invert_enthalpy(Kd, Hd, 0.0, clamp01(Cd), Td, Fld);
-        const double rho = mix(clamp01(Cd), Fld, Kd.mrho);
+        const double rho = mix(clamp01(Cd), Fld, Kd.mrho, Kd.lit);
         if (H) H[c] = Hd;
         if (T) T[c] = Td;
         if (Fl) Fl[c] = Fld;
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(kDiagThreads) diag_partial_kernel(const Domain
         const double H = pair_value(w.Hh, w.Hl), C = pair_value(w.Ch, w.Cl);
         double T, Fl;
         invert_enthalpy(Kd, H, 0.0, clamp01(C), T, Fl);
-        const double rho = mix(clamp01(C), Fl, Kd.mrho);
+        const double rho = mix(clamp01(C), Fl, Kd.mrho, Kd.lit);
         // cell volume: 1, or the radius r_i = i + 1/2 per radian (axisymmetric)
         const double vol = Kd.axi ? (double)(c % Kd.nx) + 0.5 : 1.0;
         acc[0] += vol * rho;
@@ -273,7 +275,7 @@ diag_partial_noalloc_kernel(Consts<double> Kd, const R* b, long long n, double* 
         const double H = pair_value(w.Hh, w.Hl), C = pair_value(w.Ch, w.Cl);
         double T, Fl;
         invert_enthalpy(Kd, H, 0.0, clamp01(C), T, Fl);
-        const double rho = mix(clamp01(C), Fl, Kd.mrho);
+        const double rho = mix(clamp01(C), Fl, Kd.mrho, Kd.lit);
         acc[0] += rho;
         acc[1] += H;
         acc[2] += C;
@@ -301,24 +303,59 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 double* g_noalloc_ptr[kMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kMaxDevices] = {};
+
+typedef CUresult (*ctx_get_current_fn)(CUcontext*);
+typedef CUresult (*ctx_get_id_fn)(CUcontext, unsigned long long*);
+
+// Identifier of the current CUDA context (unique for the life of the
+// process; 0 if there is none or the driver does not provide it).  The
+// driver calls are fetched through the runtime, so the library needs no link
+// against the driver library.  Called with g_noalloc_mutex held.
+unsigned long long current_context_id() {
+    static bool tried = false;
+    static ctx_get_current_fn get_current = nullptr;
+    static ctx_get_id_fn get_id = nullptr;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<ctx_get_current_fn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<ctx_get_id_fn>(f);
+        cudaGetLastError();
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS) return id;
+    return 0;
+}
 
 // Device address of g_noalloc_partials on the current device.  In host code
 // the array's name is only a host-side stand-in, never a device address, so
-// the address is resolved once per device (with that device current).
+// the address is resolved with the device current: once per device and
+// context, and again whenever the device's context has changed (after a
+// cudaDeviceReset the old address is not valid).
 int noalloc_scratch(double** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_error(EULBFS_ECUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return set_error(EULBFS_ECUDA, "device index out of range");
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_noalloc_ptr[dev] || ctx == 0 || ctx != g_noalloc_ctx[dev]) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        e = cudaGetSymbolAddress(&p, g_noalloc_partials);   // makes the context current if it was not
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             return set_error(EULBFS_ECUDA, "cudaGetSymbolAddress of the diagnostics scratch array failed");
         }
         g_noalloc_ptr[dev] = static_cast<double*>(p);
+        g_noalloc_ctx[dev] = current_context_id();
     }
     *out = g_noalloc_ptr[dev];
     return EULBFS_OK;
@@ -346,6 +383,7 @@ extern "C" int eulbfs_diagnostics_noalloc(int precision, const void* state, int 
     DomainDesc d = {};
     const eulbfs_phase* ph[3] = {&props->s, &props->l, &props->g};
     for (int k = 0; k < 3; ++k) { d.rho[k] = ph[k]->rho; d.cp[k] = ph[k]->cp; }
+    d.literal_eq7 = props->literal_eq7 ? 1 : 0;
     d.Ts = props->Ts;
     d.Tl = props->Tl;
     d.L = props->L;

@@ -26,6 +26,8 @@
 // cell centres (e_n = +-1, e_t = 0), the two cells' extrapolations half a cell
 // along t (e_n = +-1, e_t = +-1) and three points on the face itself (e_n = 0),
 // which take the mean of the two one-sided reconstructions (Eq. 54, R7).
+#include <mutex>
+
 #include "device_common.cuh"
 
 namespace eulbfs {
@@ -654,7 +656,7 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
         dfs = reinterpret_cast<const R*>(K.dFs)[c];
     }
     const R cs2 = R(1.0 / 3.0);
-    const R D = clamp01(C) * dfs;
+    const R D = solid_gate(K, C) * dfs;
     Rk[0] += Cp * T * divu;                                           // Eq. 51 row 1
     Rk[1] += u * (drx * cs2) + v * (dry * cs2) + rho * cs2 * cc.x * D;   // row 2
     Rk[2] += cs2 * (-Fl * C * dmx + rho * cc.y - rho * u * D);         // row 3 (R13)
@@ -700,7 +702,7 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
         R Tn, Fln;
         const R Cn = o.Ch + o.Cl;
         invert_enthalpy(K, o.Hh, o.Hl, clamp01(Cn), Tn, Fln);
-        const R keep = R(1) - clamp01(Cn) * (R(1) - Fln);
+        const R keep = R(1) - solid_gate(K, Cn) * (R(1) - Fln);
         o.mx *= keep;
         o.my *= keep;
     }
@@ -786,23 +788,41 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) stage_kernel(Stage
     }
 }
 
+// The dynamic shared-memory limit of stage_kernel<R> is a per-device
+// attribute: it is set once for every device the kernel is launched on, under
+// a lock, so that solvers on several devices and several host threads can
+// launch it.
+constexpr int kMaxAttrDevices = 64;
+
+template <class R>
+static cudaError_t configure_t() {
+    static std::mutex m;
+    static bool done[kMaxAttrDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxAttrDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(m);
+    if (!done[dev]) {
+        e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<R>));
+        if (e != cudaSuccess) return e;
+        done[dev] = true;
+    }
+    return cudaSuccess;
+}
+
 template <class R>
 static cudaError_t launch_t(const StageLaunch& a, int grid, cudaStream_t s) {
-    const size_t smem = sizeof(Smem<R>);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    stage_kernel<R><<<grid, NT, smem, s>>>(a);
+    cudaError_t e = configure_t<R>();
+    if (e != cudaSuccess) return e;
+    stage_kernel<R><<<grid, NT, sizeof(Smem<R>), s>>>(a);
     return cudaGetLastError();
 }
 
 template <class R>
 static int blocks_per_sm_t() {
     const size_t smem = sizeof(Smem<R>);
-    cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (configure_t<R>() != cudaSuccess) return 1;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage_kernel<R>, NT, smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;

@@ -39,7 +39,7 @@ class Props(ct.Structure):
     _fields_ = [("s", Phase), ("l", Phase), ("g", Phase), ("L", ct.c_double), ("Ts", ct.c_double),
                 ("Tl", ct.c_double), ("sigma", ct.c_double), ("xi", ct.c_double), ("Mc", ct.c_double),
                 ("tau_g", ct.c_double), ("gx", ct.c_double), ("gy", ct.c_double),
-                ("zero_solid_velocity", ct.c_int)]
+                ("zero_solid_velocity", ct.c_int), ("literal_eq7", ct.c_int)]
 
 
 class Side(ct.Structure):
@@ -97,6 +97,7 @@ SIGNATURES = [
     ("eulbfs_domain_progress", ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]),
     ("eulbfs_step", ct.c_int, [ct.c_void_p, ct.c_longlong]),
     ("eulbfs_sync", ct.c_int, [ct.c_void_p]),
+    ("eulbfs_nonfinite_domains", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int), ct.c_int, ct.POINTER(ct.c_int)]),
     ("eulbfs_fields", ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(FieldsOut)]),
     ("eulbfs_get_state", ct.c_int, [ct.c_void_p, ct.c_int] + [_DP] * 7 + [ct.POINTER(ct.c_longlong)]),
     ("eulbfs_set_state", ct.c_int, [ct.c_void_p, ct.c_int] + [_DP] * 6 + [ct.c_double, ct.c_longlong]),
@@ -145,7 +146,7 @@ def _ptr(a: Optional[np.ndarray]):
 def _props(p) -> Props:
     ph = lambda q: Phase(q.rho, q.mu, q.lam, q.cp)  # noqa: E731
     return Props(ph(p.s), ph(p.l), ph(p.g), p.L, p.Ts, p.Tl, p.sigma, p.xi, p.Mc, p.tau_g, p.gx, p.gy,
-                 int(p.zero_solid_velocity))
+                 int(p.zero_solid_velocity), int(getattr(p, "literal_eq7", 0)))
 
 
 def _bc(b) -> BC:
@@ -223,6 +224,14 @@ class Solver:
 
     def sync(self):
         _check(lib().eulbfs_sync(self._h))
+
+    def nonfinite_slots(self) -> List[int]:
+        """Slots whose own state became NaN or Inf (synchronises the stream)."""
+        cap = max(1, len(self.shapes))
+        buf = (ct.c_int * cap)()
+        n = ct.c_int()
+        _check(lib().eulbfs_nonfinite_domains(self._h, buf, cap, ct.byref(n)))
+        return [buf[k] for k in range(min(n.value, cap))]
 
     def use_graphs(self, steps: int):
         _check(lib().eulbfs_use_graphs(self._h, steps))

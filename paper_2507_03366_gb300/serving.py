@@ -11,6 +11,8 @@ so all running cases advance together in the same stage launches:
             at its own step count, its slot leaves the work list);
   retire -- finished cases have their fields copied to the host and their
             memory released; their time to solution is completion - arrival.
+            A case whose own state became NaN or Inf (its per-domain flag,
+            read after every chunk) is retired with that error at once.
 
 Results do not depend on which other cases share the launches (the per-cell
 arithmetic is independent of the batch), which the tests check bit for bit.
@@ -78,8 +80,10 @@ def serve(requests, precision: int = eulbfs.FP32C, budget_bytes: int = 0, chunk:
 
     realtime=True replays arrivals against the wall clock (arrival_s after the
     start); realtime=False admits every case as soon as it fits (a closed loop,
-    for tests).  A case that fails (e.g. a non-finite state) is retired with
-    its error and does not affect the others."""
+    for tests).  A case whose state becomes non-finite is retired with that
+    error after the chunk in which it diverged and does not affect the others.
+    A CUDA error from a launch is sticky for the whole context, so it retires
+    every running case with that error."""
     reqs = sorted(requests, key=lambda r: (r.arrival_s, r.rid))
     solver = eulbfs.Solver([], precision=precision, stream=stream)
     if budget_bytes:
@@ -121,15 +125,17 @@ def serve(requests, precision: int = eulbfs.FP32C, budget_bytes: int = 0, chunk:
                     time.sleep(max(0.0, min(pending[0].arrival_s - now(), 0.05)))
                 continue
             step_error = None
+            diverged = set()
             try:
                 solver.step(chunk)
+                diverged = set(solver.nonfinite_slots())     # one flag per case; synchronises
             except eulbfs.EulbfsError as e:
                 step_error = str(e)
-            # retire finished cases (eulbfs_fields synchronises the stream)
+            # retire finished and diverged cases
             for slot in list(running):
                 r, t_adm = running[slot]
                 done, left = solver.progress(slot)
-                if left != 0 and step_error is None:
+                if left != 0 and step_error is None and slot not in diverged:
                     continue
                 err = None
                 fields = diag = None
@@ -139,6 +145,8 @@ def serve(requests, precision: int = eulbfs.FP32C, budget_bytes: int = 0, chunk:
                     diag = solver.diag(slot)
                 except eulbfs.EulbfsError as e:
                     err = str(e)
+                if slot in diverged:
+                    err = err or "ENONFINITE: the case's state became NaN or Inf"
                 if step_error is not None and left != 0:
                     err = err or step_error
                 cell_steps += r.case.cells * done

@@ -46,6 +46,7 @@ class Props:
     gx: float = 0.0
     gy: float = 0.0
     zero_solid_velocity: int = 1
+    literal_eq7: int = 0       # 1: Eq. 5-7 exactly as printed instead of reading R1
 
 
 @dataclass

@@ -391,3 +391,32 @@ def test_film_512_long_run_fp32c_against_fp64():
     g, dg, d0g = runs[eulbfs.FP32C]
     assert dr["solid_vol"] > 0 and not dr["nonfinite"]
     check_fp32c(g, r, dg, dr, d0g, d0r)
+
+
+def test_solvers_on_two_host_threads():
+    """FP64 and FP32C solvers created and stepped from two host threads at
+    once (the stage kernel's launch set-up is per device and locked) give
+    the results of the same solvers run one after the other."""
+    import threading
+    cases = [lambda: wl.droplet(48, theta_deg=80.0, St=0.3), lambda: wl.three_phase(128, 4, St=1.0, H0=64)]
+
+    def run(make, precision, out, key):
+        s = eulbfs.Solver([make()], precision=precision)
+        s.step(60)
+        out[key] = s.fields()
+        s.close()
+
+    serial, threaded = {}, {}
+    for k, make in enumerate(cases):
+        for prec in (eulbfs.FP64, eulbfs.FP32C):
+            run(make, prec, serial, (k, prec))
+    threads = [threading.Thread(target=run, args=(make, prec, threaded, (k, prec)))
+               for k, make in enumerate(cases) for prec in (eulbfs.FP64, eulbfs.FP32C)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert set(threaded) == set(serial)
+    for key in serial:
+        for f in FIELDS:
+            assert np.array_equal(threaded[key][f], serial[key][f]), (key, f)

@@ -76,6 +76,27 @@ def test_failing_case_is_evicted_without_affecting_others():
             assert np.array_equal(o.fields[k], ref[k]), (r.rid, k)
 
 
+def test_diverged_case_is_evicted_within_one_chunk():
+    """A diverging case with a long step limit leaves after the chunk in which
+    it diverged instead of holding its slot until its last step."""
+    reqs = trace(3, seed=15)
+    bad = wl.droplet(32, theta_deg=90.0, impact_speed=0.03, name="unstable_long")
+    bad.dt = 40.0
+    chunk = 6
+    reqs.insert(1, wl.Request(77, 0.001, bad, 100000))
+    rep = serving.serve(reqs, chunk=chunk, keep_fields=True, realtime=False)
+    by_id = {o.rid: o for o in rep.outcomes}
+    assert by_id[77].error is not None and "ENONFINITE" in by_id[77].error
+    assert by_id[77].steps <= 2 * chunk, by_id[77].steps
+    for r in reqs:
+        if r.rid != 77:
+            o = by_id[r.rid]
+            assert o.error is None and o.steps == r.steps
+            ref = alone(r.case, r.steps, eulbfs.FP32C)
+            for k in FIELDS:
+                assert np.array_equal(o.fields[k], ref[k]), (r.rid, k)
+
+
 def test_realtime_trace_reports_latency():
     reqs = trace(4, seed=14)
     rep = serving.serve(reqs, chunk=8, realtime=True)

@@ -18,6 +18,7 @@ PINS = "tests/test_oracle_pins.py::"
 AXI = "tests/test_oracle_axisymmetric.py::"
 HYS = "tests/test_oracle_hysteresis.py::"
 STR = "tests/test_oracle_streaming.py::"
+BRT = "tests/test_oracle_brute_force.py::"
 
 # (name, original text, planted text, pin that must fail)
 MUTATIONS = [
@@ -60,7 +61,7 @@ MUTATIONS = [
     ("dirichlet_ghost", "2.0 * sd->Tw - vm : vm;", "sd->Tw : vm;", "test_neumann_two_phase_front"),
     ("noslip_tangential", "if (sd->flow == OR_BC_NOSLIP) return -vm;",
      "if (sd->flow == OR_BC_NOSLIP) return f == normal_f ? -vm : vm;", "test_poiseuille_profile"),
-    ("rigid_solid_R15", "const double keep = 1.0 - clamp01(s->W[4][c]) * (1.0 - Fl);", "const double keep = 1.0;",
+    ("rigid_solid_R15", "const double keep = 1.0 - solid_gate(&s->P, s->W[4][c]) * (1.0 - Fl);", "const double keep = 1.0;",
      "test_rigid_solid"),
     ("lagged_rate_R14", "s->dFs[c] = (Fs - s->Fsp[c]) / dt;", "s->dFs[c] = 0.5 * (Fs - s->Fsp[c]) / dt;",
      "test_freezing_momentum_decay"),
@@ -104,6 +105,23 @@ MUTATIONS = [
      STR + "test_phase_field_fluxes_with_steps"),
     ("streaming_hoop_step", "FE[2] += CS2 * (s->prim[P_P][q] - s->dtf * divF[1] -",
      "FE[2] += CS2 * (s->prim[P_P][q] - s->dth * divF[1] -", STR + "test_axisymmetric_radial_expansion_with_steps"),
+    # cross terms that only fields varying together expose (brute-force pin)
+    ("surrounding_feq_face_density", "feqs[a] = or_feq(a, qf[a][P_P], qf[a][P_RHO], qf[a][P_U], qf[a][P_V]);",
+     "feqs[a] = or_feq(a, qf[a][P_P], rho_f, qf[a][P_U], qf[a][P_V]);", BRT + "test_face_flux_matches_brute_force"),
+    ("feqm_surrounding_density", "feqms[a] = or_feqm(a, qf[a][P_P], rho_f, qf[a][P_U], qf[a][P_V]);",
+     "feqms[a] = or_feqm(a, qf[a][P_P], qf[a][P_RHO], qf[a][P_U], qf[a][P_V]);",
+     BRT + "test_face_flux_matches_brute_force"),
+    ("heq_face_heat_capacity",
+     "heqs[a] = or_heq(a, qh[a][P_H], qh[a][P_T], qh[a][P_CP], s->Cref, qh[a][P_U], qh[a][P_V]);",
+     "heqs[a] = or_heq(a, qh[a][P_H], qh[a][P_T], Cpf, s->Cref, qh[a][P_U], qh[a][P_V]);",
+     BRT + "test_face_flux_matches_brute_force"),
+    # Eq. 5-7 as printed (literal_eq7)
+    ("literal_liquidus_enthalpy_gated", "*Hl = P->l.cp * P->Tl + P->L;", "*Hl = *cpl * P->Tl + P->L;",
+     "test_literal_eq7_closure_values"),
+    ("literal_mixture_drops_liquid_fraction", "return Fs * gs + (1.0 - Fs) * Ct * gl", "return Fs * gs + Ct * gl",
+     "test_literal_eq7_closure_values"),
+    ("literal_sources_gated", "return P->literal_eq7 ? 1.0 : clamp01(C);", "return clamp01(C);",
+     BRT + "test_literal_eq7_matches_brute_force"),
 ]
 
 

@@ -102,6 +102,32 @@ def test_enthalpy_inversion_values():
         assert abs(t - T) < 1e-12
 
 
+def test_literal_eq7_closure_values():
+    """Eq. 5-7 exactly as printed (literal_eq7) at hand-computed points, next
+    to reading R1 where the two differ: cold gas counts as solid."""
+    P = _props(rho=(0.9, 1.0, 0.01), cp=(2.0, 4.0, 1.0), L=3.0, Ts=0.5, Tl=0.5)
+    P.literal_eq7 = 1
+    # printed: H_s = C_p,s T_s = 1, H_l = C_p,l T_l + L = 5, whatever C is
+    t, f = oracle.invert_enthalpy(P, 0.6, 0.0)          # gas below H_s: solid branch, T = H / C_p,s
+    assert abs(t - 0.3) < 1e-15 and f == 0.0
+    assert abs(oracle.mix(P, 0.0, f, 0) - 0.9) < 1e-15   # and it takes the solid density
+    t, f = oracle.invert_enthalpy(P, 7.0, 0.0)          # gas above H_l: T = T_l + (H - H_l) / C_p,g
+    assert abs(t - 2.5) < 1e-15 and f == 1.0
+    t, f = oracle.invert_enthalpy(P, 7.0, 0.5)          # liquid branch C_p = 0.5 * 4 + 0.5 * 1 = 2.5
+    assert abs(t - 1.3) < 1e-15 and f == 1.0
+    t, f = oracle.invert_enthalpy(P, 3.0, 0.5)          # mushy: F_l = (3 - 1) / (5 - 1)
+    assert abs(f - 0.5) < 1e-15 and abs(t - 0.5) < 1e-15
+    # Eq. 7 with F_s = 0.5, C = 0.5: 0.5 * 0.9 + 0.5 * 0.5 * 1.0 + 0.5 * 0.5 * 0.01
+    assert abs(oracle.mix(P, 0.5, 0.5, 0) - 0.7025) < 1e-15
+    assert abs(oracle.enthalpy_of(P, 0.3, 1.0, 0.0) - 0.6) < 1e-15
+    # reading R1 on the same gas cell: C_p,g in both branches, so H_s = 0.5,
+    # H_l = 3.5 and H = 0.6 is mushy with F_l = 0.1 / 3; the density stays the gas's
+    P.literal_eq7 = 0
+    t, f = oracle.invert_enthalpy(P, 0.6, 0.0)
+    assert abs(f - 0.1 / 3.0) < 1e-15 and abs(t - 0.5) < 1e-15
+    assert abs(oracle.mix(P, 0.0, f, 0) - 0.01) < 1e-15
+
+
 def test_property_mixing():
     P = _props(rho=(0.9, 1.0, 0.001), mu=(0.3, 0.2, 0.002), lam=(2.2, 0.56, 0.02), cp=(2.0, 4.0, 1.0))
     for which, vals in enumerate([(0.9, 1.0, 0.001), (0.3, 0.2, 0.002), (2.2, 0.56, 0.02), (2.0, 4.0, 1.0)]):
