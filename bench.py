@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import copy
+import hashlib
 import json
 import os
 import statistics
@@ -31,27 +32,32 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-BYTES_PER_CELL_STEP = {1: 244, 0: 352}    # algorithmic HBM bytes per cell per time step (FP32C, FP64)
 STAGES = 3
-# Per cell and stage of the FP32C stage kernel, from the ncu counters of one
-# capture of each geometry (24 domains, 2.32 M cells, stages 0-2): FP32
-# operations (FFMA counted as 2) and warp instructions issued.  They are the
-# formulation's arithmetic and the kernel's instruction stream, so they change
-# only with the face/cell algebra or the code.
-FP32_FLOPS_PER_CELL_STAGE = {"rz": 939, "xy": 901}
-WARP_INST_PER_CELL_STAGE = {"rz": 43.1, "xy": 41.7}
-# DRAM bytes per cell per launch of the stage kernel (ncu, average of the 3
-# stages of the same capture, scaled by cells).
-DRAM_BYTES_PER_CELL_LAUNCH = 64.4
-# FP64 operations per cell per stage of the FP64 stage kernel (DFMA counted as
-# 2), from the ncu counters of one capture of each geometry.
-FP64_FLOPS_PER_CELL_STAGE = {"rz": 1035, "xy": 958}
+# Algorithmic HBM bytes per cell and time step of the FP32C path:
+#  - compulsory: the state read once and written once per step, 7 planes of
+#    4 B each way plus F_s^{n-1} read and written (a fully fused step);
+#  - stage-by-stage: what a kernel per Runge-Kutta stage must move (stage
+#    input, W^n at stages 2 and 3, output; F_s and dF_s/dt).
+BYTES_COMPULSORY = {1: 64, 0: 96}
+BYTES_STAGE_BY_STAGE = {1: 244, 0: 352}
+# Counters of the FP32C and FP64 stage kernels from ncu captures (24 domains,
+# 2.32 M cells, stages 0-2 of one step), per cell and stage: FP32 (FP64)
+# operations with an FMA counted as 2, warp instructions issued, and DRAM
+# bytes per launch.  They belong to one version of the kernel's sources: the
+# SHA-256 of stage.cu + device_common.cuh + eulbfs_internal.h.  When the
+# sources change, the counters are reported as stale (null) until they are
+# captured again.
+KERNEL_SOURCES = ("stage.cu", "device_common.cuh", "eulbfs_internal.h")
+COUNTERS = {
+    "sources_sha256": "4b42f2a81d586bd7cf82e5af8d2c4d717f6aeee91f3432563f568c1480f609ba",
+    "fp32_flops_per_cell_stage": {"rz": 939, "xy": 901},
+    "warp_inst_per_cell_stage": {"rz": 43.1, "xy": 41.7},
+    "dram_bytes_per_cell_launch": {"rz": 64.4, "xy": 64.4},
+    "fp64_flops_per_cell_stage": {"rz": 1035, "xy": 958},
+}
 # Streaming steps (dt_h, dt_f, dt_g) of the general-face-path leg.
 GEN_STEPS = (0.3, 0.4, 0.3)
-# Peaks from unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x SM clock;
-# 4 warp instructions issued per SM per clock (one per scheduler); 2 FP64
-# FMA lanes per SM (ncu's sustained DFMA peak) x 2 flops x SM clock.
-SMS, FP32_LANES_PER_SM, ISSUE_PER_SM_CLK, FP64_LANES_PER_SM = 152, 128, 4, 2
+METRIC = "GCUPS coupled EULBFS step, FP32 batched vs FP64 plain; p50/p99 solve latency"
 
 
 def parse():
@@ -68,11 +74,15 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=30)
     ap.add_argument("--gen-steps", type=int, default=200,
                     help="steps of the general-streaming-step leg (0: skip)")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=8.0,
+                    help="seconds of oracle work per CPU-baseline leg (one thread, all cores)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve", type=int, default=500, help="requests in the serving leg (0: skip)")
+    ap.add_argument("--serve-fp64", type=int, default=50,
+                    help="requests of the trace also served as sequential FP64 solves (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=4.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FMA-peak measurement")
     ap.add_argument("--geometry", default="rz", choices=["rz", "xy"],
                     help="rz: axisymmetric (r, z) droplet domains; xy: planar 2-D")
     return ap.parse_args()
@@ -117,7 +127,7 @@ def barrier(world: int):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during a timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -168,16 +178,42 @@ def measured_peaks():
         return None
 
 
+def kernel_sources_sha256() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2507_03366_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def counters_current() -> bool:
+    """The ncu counters above were taken on the kernel as it is now."""
+    return kernel_sources_sha256() == COUNTERS["sources_sha256"]
+
+
 def workload(n_domains: int, seed: int, geometry: str = "rz"):
     from paper_2507_03366_gb300 import workloads as wl
     return wl.static_droplet_batch(n_domains, seed=seed, axisymmetric=geometry == "rz")
 
 
-def cpu_baseline(cases, seconds: float) -> dict:
-    """The oracle as it stands, single-threaded, on the first domains of the
-    batch for a bounded number of steps (a partial-run rate)."""
+def host_cores() -> dict:
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Model name", "Architecture", "CPU(s)", "Thread(s) per core"):
+                info[k.strip()] = v.strip()
+    except Exception:
+        pass
+    return info
+
+
+def oracle_rate(case, seconds: float, threads: int) -> dict:
+    """The oracle as it stands on one domain for about `seconds` of work with
+    `threads` host threads; GCUPS over the steps it finished."""
     import oracle
-    case = min(cases, key=lambda c: c.cells)
+    used = oracle.set_threads(threads)
     s = oracle.OracleSolver(case)
     s.step(1)
     t0 = time.perf_counter()
@@ -186,20 +222,23 @@ def cpu_baseline(cases, seconds: float) -> dict:
         s.step(2)
         steps += 2
     el = time.perf_counter() - t0
-    return {"value": case.cells * steps / el / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} steps of domain {case.name} ({case.nx}x{case.ny}) of the batch, "
-                      f"single-threaded FP64 oracle, {el:.1f} s"}
+    return {"value": case.cells * steps / el / 1e9, "unit": "GCUPS", "cores": used, "steps": steps,
+            "seconds": el}
 
 
-METRIC = "GCUPS coupled EULBFS step, FP32 batched vs FP64 plain; p50/p99 solve latency"
-
-
-def binding_roof(bytes_per_launch: float, flops_per_launch: float, hbm_gbs: float, fp32_tflops: float) -> str:
-    """The roof that bounds a launch: the one whose minimum time (bytes over
-    bandwidth, or flops over the FP32 rate) is the longer; "hbm" on a tie."""
-    t_mem = bytes_per_launch / (hbm_gbs * 1e9)
-    t_alu = flops_per_launch / (fp32_tflops * 1e12)
-    return "hbm" if t_mem >= t_alu else "alu"
+def cpu_baseline(cases, seconds: float) -> dict:
+    """The FP64 oracle on the smallest domain of the batch, single-threaded and
+    on every host core (a partial-run rate: the oracle is a baseline, not a
+    target)."""
+    case = min(cases, key=lambda c: c.cells)
+    one = oracle_rate(case, seconds, 1)
+    allc = oracle_rate(case, seconds, os.cpu_count() or 1)
+    return {"value": allc["value"], "unit": "GCUPS", "cores": allc["cores"], "kind": "oracle",
+            "sample": f"{allc['steps']} steps of domain {case.name} ({case.nx}x{case.ny}) of the batch, FP64 oracle "
+                      f"on {allc['cores']} host threads (OpenMP over rows and faces), {allc['seconds']:.1f} s",
+            "single_thread": {"value": one["value"], "unit": "GCUPS", "cores": 1,
+                              "sample": f"{one['steps']} steps of the same domain, {one['seconds']:.1f} s"},
+            "host": host_cores()}
 
 
 def workload_config(cases, world: int, args) -> dict:
@@ -216,6 +255,63 @@ def workload_config(cases, world: int, args) -> dict:
                    f"working set {cells * 28 * 3 / 1e6:.0f} MB, not larger than L2 (129 MB)")}
 
 
+def measure_fma_peaks(stream) -> dict:
+    """FP32 (scalar and packed f32x2) and FP64 FMA throughput of this GPU,
+    each from one launch of about 0.2 s after a short calibration launch,
+    with the SM clock sampled during the launches."""
+    import torch
+    from paper_2507_03366_gb300 import eulbfs
+    out = {}
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for name, kind in (("fp32", eulbfs.PEAK_FP32), ("fp32x2", eulbfs.PEAK_FP32X2), ("fp64", eulbfs.PEAK_FP64)):
+        probe = eulbfs.peak_fma(kind, 2000, stream)
+        iters = max(2000, int(2000 * 200.0 / max(probe["ms"], 1e-3)))
+        r = eulbfs.peak_fma(kind, iters, stream)
+        out[name] = {"tflops": r["flops_per_s"] / 1e12, "fma_warp_inst_per_s": r["fma_warp_inst_per_s"],
+                     "ms": r["ms"], "iters": iters}
+    out["clocks"] = clocks.stop()
+    return out
+
+
+def roofline(cells, geometry, per_launch_ms, hbm_gbs, peaks) -> dict:
+    """The stage kernel's roofs; the top level names the one with the largest
+    fraction, which is the one the kernel meets first."""
+    current = counters_current()
+    s = per_launch_ms * 1e-3
+    hbm = {}
+    for key, b, what in (("compulsory", BYTES_COMPULSORY[1], "state read and written once per step"),
+                         ("stage_by_stage", BYTES_STAGE_BY_STAGE[1], "a kernel per Runge-Kutta stage")):
+        ach = b / STAGES * cells / s / 1e9
+        hbm[key] = {"bytes_per_cell_step": b, "meaning": what, "achieved": ach, "peak": hbm_gbs, "unit": "GB/s",
+                    "frac": ach / hbm_gbs}
+    dram = COUNTERS["dram_bytes_per_cell_launch"][geometry] * cells if current else None
+    hbm["dram_measured"] = {"bytes_per_cell_launch": COUNTERS["dram_bytes_per_cell_launch"][geometry] if current else None,
+                            "achieved": dram / s / 1e9 if dram else None, "peak": hbm_gbs, "unit": "GB/s",
+                            "frac": dram / s / 1e9 / hbm_gbs if dram else None}
+    roofs = {"hbm_" + k: dict(v, bound="hbm", peak_source="measured copy bandwidth (MEASURED_PEAKS.json)")
+             for k, v in hbm.items()}
+    if peaks:
+        fp32_peak = max(peaks["fp32"]["tflops"], peaks["fp32x2"]["tflops"])
+        issue_peak = peaks["fp32"]["fma_warp_inst_per_s"]
+        flops = COUNTERS["fp32_flops_per_cell_stage"][geometry] * cells if current else None
+        inst = COUNTERS["warp_inst_per_cell_stage"][geometry] * cells if current else None
+        roofs["fp32"] = {"bound": "alu", "flops_per_cell_stage": COUNTERS["fp32_flops_per_cell_stage"][geometry]
+                         if current else None, "achieved": flops / s / 1e12 if flops else None, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": flops / s / 1e12 / fp32_peak if flops else None,
+                         "peak_source": "measured this run: FMA-chain kernel, best of scalar and f32x2"}
+        roofs["issue"] = {"bound": "alu", "warp_inst_per_cell_stage": COUNTERS["warp_inst_per_cell_stage"][geometry]
+                          if current else None, "achieved": inst / s if inst else None, "peak": issue_peak,
+                          "unit": "warp-inst/s", "frac": inst / s / issue_peak if inst else None,
+                          "peak_source": "measured this run: warp instructions per second of the scalar FP32 "
+                                         "FMA-chain kernel (one FFMA per lane per instruction)"}
+    top = max((v for v in roofs.values() if v.get("frac") is not None), key=lambda v: v["frac"])
+    return {"bound": top["bound"], "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
+            "frac": top["frac"], "traffic": dram, "binding_roof": next(k for k, v in roofs.items() if v is top),
+            "kernel": "eulbfs::stage_kernel<float>", "avg_launch_ms": per_launch_ms,
+            "counters_current": current, "roofs": roofs}
+
+
 def run_reference(args):
     """The FP64 CPU oracle, as it stands, on the machine's host cores: each step is
     a bounded sample of the workload (one domain of the batch)."""
@@ -225,25 +321,39 @@ def run_reference(args):
     cases = workload(args.domains, rank_seed(args.seed, 0), args.geometry)
     import oracle
     case = min(cases, key=lambda c: c.cells)
+    cores = oracle.set_threads(os.cpu_count() or 1)
     s = oracle.OracleSolver(case)
     for _ in range(args.warmup):
         s.step(1)
     # bounded: about two minutes of oracle work for the whole timed part
-    steps = max(1, min(args.steps, int(120.0 * 1.2e5 / case.cells)))
+    probe_t = time.perf_counter()
+    s.step(2)
+    per_step = (time.perf_counter() - probe_t) / 2
+    steps = max(1, min(args.steps, int(120.0 / max(per_step, 1e-6))))
     t0 = time.perf_counter()
     s.step(steps)
     el = time.perf_counter() - t0
     value = case.cells * steps / el / 1e9
     sample = (f"{steps} steps of domain {case.name} ({case.nx}x{case.ny}) of the batch, "
-              f"single-threaded FP64 oracle, {el:.1f} s")
+              f"FP64 oracle on {cores} host threads, {el:.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": args.gpus,
             "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(cases, 1, args),
-            "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def timed_steps(solver, stream, steps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
 
 
 def main():
@@ -263,12 +373,15 @@ def main():
     cases = workload(args.domains, rank_seed(args.seed, rank), args.geometry)
     cells = sum(c.cells for c in cases)
     stream = torch.cuda.Stream()
+    peaks = None if args.no_peaks else measure_fma_peaks(stream.cuda_stream)
     sol = eulbfs.Solver(cases, precision=eulbfs.FP32C, stream=stream.cuda_stream)
+    tuning = None
     if args.tile == 0:
         # the autotuner times each candidate height on the live batch (its
         # steps are part of the warm-up); every solver below uses the winner
         args.tile, _ = sol.autotune(5)
         args.autotuned = True
+        tuning = {str(k): v for k, v in sorted(sol.autotune_report().items())}
     sol.set_tile(args.tile)
     if args.graph:
         sol.use_graphs(args.graph)
@@ -296,35 +409,13 @@ def main():
     value = total_cells * args.steps / (ms_max * 1e-3) / 1e9
     launches = STAGES * args.steps
 
-    # ---- roofline of the stage kernel (the only kernel in the region) --------
-    # Arithmetic intensity ~940 flop / 81.3 B = 11.6 flop/B sits at the machine
-    # balance (80.5 TFLOP/s / 6.78 TB/s = 11.9 flop/B): the binding roof is the
-    # one whose minimum launch time is the longer; the other is reported beside
-    # it, with the instruction-issue rate that the kernel actually meets.
-    peaks = measured_peaks()
-    hbm = peaks["hbm_gbs"] if peaks else 6800.0
-    clk_mhz = (peaks or {}).get("sm_max_mhz", 2070.0)
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12      # TFLOP/s
-    per_launch_ms = ms / launches
-    alg_bytes = BYTES_PER_CELL_STEP[1] / STAGES * cells
-    achieved_gbs = alg_bytes / (per_launch_ms * 1e-3) / 1e9
-    flops = FP32_FLOPS_PER_CELL_STAGE[args.geometry] * cells
-    achieved_tf = flops / (per_launch_ms * 1e-3) / 1e12
-    issue_peak = SMS * ISSUE_PER_SM_CLK * clk_mhz * 1e6
-    issue = WARP_INST_PER_CELL_STAGE[args.geometry] * cells / (per_launch_ms * 1e-3)
-    alu = {"achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved_tf / fp32_peak,
-           "peak_source": "unit counts x max SM clock (152 x 128 x 2 x %.0f MHz)" % clk_mhz,
-           "flops_per_launch": flops}
-    mem = {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
-           "peak_source": "measured" if peaks else "fallback", "algorithmic_bytes_per_launch": alg_bytes}
-    hbm_bound = binding_roof(alg_bytes, flops, hbm, fp32_peak) == "hbm"
-    top, other = (mem, alu) if hbm_bound else (alu, mem)
-    roofline = {"bound": "hbm" if hbm_bound else "alu", **top, "traffic": DRAM_BYTES_PER_CELL_LAUNCH * cells,
-                "kernel": "eulbfs::stage_kernel<float>", "avg_launch_ms": per_launch_ms,
-                ("alu" if hbm_bound else "hbm"): other,
-                "issue": {"achieved": issue, "peak": issue_peak, "unit": "warp-inst/s", "frac": issue / issue_peak,
-                          "peak_source": "152 SMs x 4 schedulers x %.0f MHz" % clk_mhz,
-                          "warp_inst_per_cell_stage": WARP_INST_PER_CELL_STAGE[args.geometry]}}
+    mp = measured_peaks()
+    hbm = mp["hbm_gbs"] if mp else 6800.0
+    roof = roofline(cells, args.geometry, ms / launches, hbm, peaks)
+    if not mp:
+        for v in roof["roofs"].values():
+            if v.get("unit") == "GB/s":
+                v["peak_source"] = "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
 
     # ---- FP64 plain GPU step on the same workload ------------------------------
     fp64 = None
@@ -333,22 +424,17 @@ def main():
         s64.set_tile(args.tile)
         s64.step(2)
         s64.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s64.step(args.fp64_steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1)
+        ms64 = timed_steps(s64, stream, args.fp64_steps)
         fp64 = {"value": cells * args.fp64_steps / (ms64 * 1e-3) / 1e9, "unit": "GCUPS",
                 "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps}
-        f64 = FP64_FLOPS_PER_CELL_STAGE[args.geometry]
-        if f64:
-            # the FP64 step is bound by the FP64 pipe (85 % busy in ncu)
-            fp64_peak = SMS * FP64_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
+        if peaks and counters_current():
+            # the FP64 step is bound by the FP64 pipe
+            f64 = COUNTERS["fp64_flops_per_cell_stage"][args.geometry]
             ach64 = f64 * cells * STAGES * args.fp64_steps / (ms64 * 1e-3) / 1e12
-            fp64["roofline"] = {"bound": "alu", "achieved": ach64, "peak": fp64_peak, "unit": "TFLOP/s",
-                                "frac": ach64 / fp64_peak, "kernel": "eulbfs::stage_kernel<double>",
-                                "peak_source": "unit counts x max SM clock (152 x 2 x 2 x %.0f MHz)" % clk_mhz}
+            fp64["roofline"] = {"bound": "alu", "achieved": ach64, "peak": peaks["fp64"]["tflops"], "unit": "TFLOP/s",
+                                "frac": ach64 / peaks["fp64"]["tflops"], "kernel": "eulbfs::stage_kernel<double>",
+                                "flops_per_cell_stage": f64,
+                                "peak_source": "measured this run: FP64 FMA-chain kernel"}
         s64.close()
 
     # ---- the same batch with per-distribution streaming steps (reading R26) ----
@@ -364,12 +450,7 @@ def main():
         sg.set_tile(args.tile)
         sg.step(3)
         sg.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sg.step(args.gen_steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        msg = e0.elapsed_time(e1)
+        msg = timed_steps(sg, stream, args.gen_steps)
         gv = cells * args.gen_steps / (msg * 1e-3) / 1e9
         gen = {"value": gv, "unit": "GCUPS", "steps": args.gen_steps, "ms_per_step": msg / args.gen_steps,
                "dt_stream_hfg": list(GEN_STEPS),
@@ -419,15 +500,25 @@ def main():
         from paper_2507_03366_gb300 import workloads as wl
         reqs = wl.impact_requests(args.serve, seed=5 + 1000 * rank, axisymmetric=args.geometry == "rz",
                                   hysteresis=True)
-        rep = serving.serve(reqs, precision=eulbfs.FP32C, budget_bytes=int(args.serve_budget_gb * 2 ** 30),
-                            chunk=16, stream=stream.cuda_stream, realtime=True)
+        budget = int(args.serve_budget_gb * 2 ** 30)
+        rep = serving.serve(reqs, precision=eulbfs.FP32C, budget_bytes=budget, chunk=16,
+                            stream=stream.cuda_stream, realtime=True)
         serving_out = rep.summary()
         serving_out["arrival_rate_hz"] = 20.0
         serving_out["workload"] = ("droplet impact on a cold plate, sides U[256,1024]/32, We U[10,200], "
                                    "Re U[100,2000], St U[0.05,0.5], drop released 0.1 side above the plate, end time t U/D = 0.015, "
                                    "plate angles theta_eq 82 / theta_adv 100 / theta_r 39 deg (hysteresis wall)")
-        if fp64:
-            serving_out["fp64_sequential_s_est"] = rep.cell_steps / (fp64["value"] * 1e9)
+        if args.serve_fp64 > 0:
+            # the first requests of the same trace (same arrival times), served
+            # as sequential FP64 solves (one case on the device at a time) and
+            # with FP32C continuous batching
+            sub = reqs[:args.serve_fp64]
+            r64 = serving.serve(sub, precision=eulbfs.FP64, budget_bytes=budget, chunk=16,
+                                stream=stream.cuda_stream, realtime=True, resident_cap=1)
+            r32 = serving.serve(sub, precision=eulbfs.FP32C, budget_bytes=budget, chunk=16,
+                                stream=stream.cuda_stream, realtime=True)
+            serving_out["subset"] = {"requests": len(sub), "fp64_sequential": r64.summary(),
+                                     "fp32c_batched": r32.summary()}
 
     if rank != 0:
         if world > 1:
@@ -441,7 +532,9 @@ def main():
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (H, C compensated hi/lo)", "data": "synthetic",
         "config": workload_config(cases, world, args),
-        "roofline": roofline,
+        "roofline": roof,
+        "peaks": peaks,
+        "autotune_ms_per_step": tuning,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

@@ -318,6 +318,12 @@ int eulbfs_diagnostics_noalloc(int precision, const void* state, int nx, int ny,
  * failing step returns its error and leaves the height unchanged. */
 int eulbfs_autotune(eulbfs_solver* s, int steps_per_candidate, int* best_rows, float* best_ms_per_step);
 
+/* The candidates the last eulbfs_autotune of this solver timed: up to `cap`
+ * heights (rows) and their best milliseconds per step; *n receives how many
+ * it timed (0 before any autotune).  Errors: EINVAL (null solver or n,
+ * cap < 0, null arrays with cap > 0). */
+int eulbfs_autotune_report(const eulbfs_solver* s, int* rows, float* ms_per_step, int cap, int* n);
+
 void eulbfs_destroy(eulbfs_solver* s);
 
 /* Message of the last failed call on this thread ("" if none). */

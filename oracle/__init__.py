@@ -35,8 +35,12 @@ def build(force: bool = False) -> str:
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-fPIC", "-shared",
-                               "-D_DEFAULT_SOURCE", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-fPIC", "-shared", "-D_DEFAULT_SOURCE"]
+        # OpenMP over independent loops where the compiler has it (same
+        # results for any thread count); a plain build otherwise
+        r = subprocess.run(base + ["-fopenmp", "-o", tmp, _SRC, "-lm"], capture_output=True)
+        if r.returncode != 0:
+            subprocess.check_call(base + ["-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -111,6 +115,9 @@ def lib():
             L.or_face_flux.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, _DP]
             L.or_residual.argtypes = [ct.c_void_p, _DP]
             L.or_get_muc.argtypes = [ct.c_void_p, _DP]
+            L.or_set_threads.argtypes = [ct.c_int]
+            L.or_set_threads.restype = ct.c_int
+            L.or_set_threads(1)     # single-threaded unless a caller asks for more
             _lib = L
     return _lib
 
@@ -129,6 +136,12 @@ def bc_struct(b) -> BC:
     sd = lambda q: Side(q.thermal, q.flow, q.phase, q.Tw, q.theta_deg,  # noqa: E731
                         getattr(q, "theta_adv_deg", q.theta_deg), getattr(q, "theta_rec_deg", q.theta_deg))
     return BC(sd(b.xlo), sd(b.xhi), sd(b.ylo), sd(b.yhi))
+
+
+def set_threads(n: int) -> int:
+    """Host threads the oracle's independent loops use (OpenMP builds);
+    returns the count in use.  Results are bitwise the same for any count."""
+    return lib().or_set_threads(int(n))
 
 
 # ---- equilibria and closure, exposed for the pin tests ----

@@ -23,6 +23,16 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Loops whose iterations write disjoint elements may run on several host
+ * threads (OpenMP, when the oracle is built with it).  Nothing is reduced
+ * across threads, so the results are bitwise the same for any thread count. */
+#ifdef _OPENMP
+#include <omp.h>
+#define OMP_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define OMP_FOR
+#endif
+
 #define NG 2              /* ghost ring width */
 #define CS2 (1.0 / 3.0)   /* cs^2 = c^2/3 with lattice speed c = 1 */
 
@@ -186,6 +196,7 @@ double or_geq(int a, double C, double muc, double Qg, double u, double v) {
 /* ------------------------------------------------------------------ */
 
 static void derive_interior(or_solver* s, double* const W[5]) {
+    OMP_FOR
     for (int j = 0; j < s->ny; ++j)
         for (int i = 0; i < s->nx; ++i) {
             const int c = j * s->nx + i, q = PI(s, i, j);
@@ -279,6 +290,7 @@ static void fill_ghosts(or_solver* s, const int* fields, int nf) {
     const int nx = s->nx, ny = s->ny;
     const int perx = s->B.xlo.thermal == OR_BC_PERIODIC;
     const int pery = s->B.ylo.thermal == OR_BC_PERIODIC;
+    OMP_FOR
     for (int j = 0; j < ny; ++j)
         for (int k = 1; k <= NG; ++k) {
             const int gl = -k, gh = nx - 1 + k;
@@ -293,6 +305,7 @@ static void fill_ghosts(or_solver* s, const int* fields, int nf) {
                 s->prim[f][PI(s, gh, j)] = perx ? vh : ghost_value(s, &s->B.xhi, f, k, P_U, vh, ch);
             }
         }
+    OMP_FOR
     for (int i = -NG; i < nx + NG; ++i)
         for (int k = 1; k <= NG; ++k) {
             const int gl = -k, gh = ny - 1 + k;
@@ -313,6 +326,7 @@ static void fill_ghosts(or_solver* s, const int* fields, int nf) {
  * 5-point Laplacian (R6), on interior cells; ghosts are then mirrored. */
 static void compute_muc(or_solver* s) {
     const double* C = s->prim[P_C];
+    OMP_FOR
     for (int j = 0; j < s->ny; ++j)
         for (int i = 0; i < s->nx; ++i) {
             const int q = PI(s, i, j);
@@ -334,6 +348,7 @@ static void compute_muc(or_solver* s) {
 
 /* Central differences (R6) on interior cells and ghost layer 1. */
 static void compute_gradients(or_solver* s) {
+    OMP_FOR
     for (int f = 0; f < NPRIM; ++f)
         for (int j = -1; j <= s->ny; ++j)
             for (int i = -1; i <= s->nx; ++i) {
@@ -482,12 +497,15 @@ static void face_flux(const or_solver* s, int dir, int i, int j, double out[6]) 
 static void residual(or_solver* s, double* const W[5], double* const R[5]) {
     const int nx = s->nx, ny = s->ny;
     prepare(s, W);
+    OMP_FOR
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i <= nx; ++i) face_flux(s, 0, i, j, &s->fx[(j * (nx + 1) + i) * 6]);
+    OMP_FOR
     for (int j = 0; j <= ny; ++j)
         for (int i = 0; i < nx; ++i) face_flux(s, 1, i, j, &s->fy[(j * nx + i) * 6]);
 
     const double kv = 1.0 - s->P.s.rho / s->P.l.rho;   /* (1 - rho_s/rho_l) */
+    OMP_FOR
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             const int c = j * nx + i, q = PI(s, i, j);
@@ -537,6 +555,7 @@ static void residual(or_solver* s, double* const W[5], double* const R[5]) {
 static void project_solid(or_solver* s) {
     if (!s->P.zero_solid_velocity) return;
     const int n = s->nx * s->ny;
+    OMP_FOR
     for (int c = 0; c < n; ++c) {
         double T, Fl;
         or_invert_enthalpy(&s->P, s->W[0][c], s->W[4][c], &T, &Fl);
@@ -652,6 +671,7 @@ int or_step(or_solver* s, long long nsteps) {
     const double dt = s->N.dt;
     for (long long it = 0; it < nsteps; ++it) {
         /* R14: lagged dF_s/dt from the last two time levels, fixed over the stages */
+        OMP_FOR
         for (int c = 0; c < n; ++c) {
             double T, Fl;
             or_invert_enthalpy(&s->P, s->W[0][c], s->W[4][c], &T, &Fl);
@@ -663,17 +683,20 @@ int or_step(or_solver* s, long long nsteps) {
         /* Eq. 58, stage 1 */
         residual(s, s->W, s->R);
         for (int k = 0; k < 5; ++k)
+            OMP_FOR
             for (int c = 0; c < n; ++c) s->W[k][c] = s->Wn[k][c] + dt * s->R[k][c];
         project_solid(s);
         /* stage 2 */
         residual(s, s->W, s->R);
         for (int k = 0; k < 5; ++k)
+            OMP_FOR
             for (int c = 0; c < n; ++c)
                 s->W[k][c] = 0.75 * s->Wn[k][c] + 0.25 * s->W[k][c] + 0.25 * dt * s->R[k][c];
         project_solid(s);
         /* stage 3 */
         residual(s, s->W, s->R);
         for (int k = 0; k < 5; ++k)
+            OMP_FOR
             for (int c = 0; c < n; ++c)
                 s->W[k][c] = (1.0 / 3.0) * s->Wn[k][c] + (2.0 / 3.0) * s->W[k][c] +
                              (2.0 / 3.0) * dt * s->R[k][c];
@@ -761,4 +784,14 @@ void or_get_muc(or_solver* s, double* muc) {
     prepare(s, s->W);
     for (int j = 0; j < s->ny; ++j)
         for (int i = 0; i < s->nx; ++i) muc[j * s->nx + i] = s->prim[P_MUC][PI(s, i, j)];
+}
+
+int or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

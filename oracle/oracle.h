@@ -132,6 +132,11 @@ void or_residual(or_solver* s, double* out);
 /* Chemical potential mu_c (Sec. 2.3.1, reading R5) of the current state, nx*ny. */
 void or_get_muc(or_solver* s, double* muc);
 
+/* Host threads for the loops whose iterations are independent (OpenMP
+ * builds; n <= 0 keeps the current count).  Returns the count in use (1
+ * without OpenMP).  Results do not depend on it. */
+int or_set_threads(int n);
+
 #ifdef __cplusplus
 }
 #endif

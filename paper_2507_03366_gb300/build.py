@@ -1,6 +1,7 @@
 """Build libeulbfs.so (sm_103a) in-tree with nvcc.
 
-The two translation units (kernels, host API) compile in parallel; the
+The translation units (stage kernel, auxiliary kernels, host API, FMA
+peaks) compile in parallel; the
 result lands in ``paper_2507_03366_gb300/_build/libeulbfs.so``.  Run as a
 module (``python -m paper_2507_03366_gb300.build``) or call ``build()``.
 """
@@ -17,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libeulbfs.so")
-SOURCES = ["stage.cu", "kernels.cu", "api.cu"]
+SOURCES = ["stage.cu", "kernels.cu", "api.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,7 +38,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "eulbfs.h")]
+    inc = os.path.join(ROOT, "include")
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(inc, f) for f in os.listdir(inc)]
     return any(os.path.getmtime(p) > t for p in deps)
 
 

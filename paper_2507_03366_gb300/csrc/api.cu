@@ -5,9 +5,11 @@
 // intermediate Runge-Kutta stages), F_s of the previous step and the lagged
 // dF_s/dt.  The active domains form one tile work list; a time step is three
 // launches of the stage kernel over that list (Eq. 58), optionally replayed
-// from a captured CUDA graph.  Domains can be added and removed between steps
+// from a captured CUDA graph; each stage launch and each graph replay is an
+// NVTX range for profilers.  Domains can be added and removed between steps
 // (continuous batching) under a device-memory budget.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>   // header-only: ranges cost a pointer test unless a profiler is attached
 
 #include <algorithm>
 #include <cmath>
@@ -183,6 +185,10 @@ struct eulbfs_solver {
     int graph_steps = 0;
     cudaGraphExec_t graph = nullptr;
     bool graph_valid = false;
+    // the last eulbfs_autotune: candidate heights and their best ms per step
+    int tune_n = 0;
+    int tune_rows[8] = {};
+    float tune_ms[8] = {};
 };
 
 namespace {
@@ -248,9 +254,12 @@ int launch_step_direct(eulbfs_solver* s) {
     a.nitems = s->nitems;
     a.seg = s->seg;
     a.flag = s->d_flag;
+    static const char* const kStageRange[3] = {"eulbfs RK stage 1", "eulbfs RK stage 2", "eulbfs RK stage 3"};
     for (int st = 0; st < 3; ++st) {
         a.stage = st;
+        nvtxRangePushA(kStageRange[st]);
         cudaError_t e = launch_stage(s->precision, a, s->grid, s->stream);
+        nvtxRangePop();
         if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
     }
     return EULBFS_OK;
@@ -532,8 +541,15 @@ int eulbfs_autotune(eulbfs_solver* s, int steps_per_candidate, int* best_rows, f
             if (cand_ms[k] == 0.f || ms < cand_ms[k]) cand_ms[k] = ms;
         }
     }
-    for (int k = 0; k < kNC; ++k)
+    s->tune_n = 0;
+    for (int k = 0; k < kNC; ++k) {
         if (cand_ms[k] > 0.f && (best_ms == 0.f || cand_ms[k] < best_ms)) { best_ms = cand_ms[k]; best = kCandidates[k]; }
+        if (cand_ms[k] > 0.f && s->tune_n < 8) {
+            s->tune_rows[s->tune_n] = kCandidates[k];
+            s->tune_ms[s->tune_n] = cand_ms[k];
+            ++s->tune_n;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     s->graph_steps = saved_graph;
@@ -545,6 +561,16 @@ int eulbfs_autotune(eulbfs_solver* s, int steps_per_candidate, int* best_rows, f
     eulbfs_set_tile(s, best);
     if (best_rows) *best_rows = best;
     if (best_ms_per_step) *best_ms_per_step = best_ms;
+    return EULBFS_OK;
+}
+
+int eulbfs_autotune_report(const eulbfs_solver* s, int* rows, float* ms_per_step, int cap, int* n) {
+    if (!s || !n || cap < 0 || (cap > 0 && (!rows || !ms_per_step))) return fail(EULBFS_EINVAL, "bad arguments");
+    for (int k = 0; k < s->tune_n && k < cap; ++k) {
+        rows[k] = s->tune_rows[k];
+        ms_per_step[k] = s->tune_ms[k];
+    }
+    *n = s->tune_n;
     return EULBFS_OK;
 }
 
@@ -574,7 +600,10 @@ int eulbfs_step(eulbfs_solver* s, long long n) {
         if (s->graph_steps > 0) {
             if (!s->graph_valid && left >= s->graph_steps) capture_graph(s);
             while (s->graph_valid && left >= s->graph_steps) {
-                CK(cudaGraphLaunch(s->graph, s->stream), "graph launch");
+                nvtxRangePushA("eulbfs graph replay");
+                const cudaError_t ge = cudaGraphLaunch(s->graph, s->stream);
+                nvtxRangePop();
+                CK(ge, "graph launch");
                 left -= s->graph_steps;
             }
         }

@@ -109,6 +109,8 @@ SIGNATURES = [
     ("eulbfs_use_graphs", ct.c_int, [ct.c_void_p, ct.c_int]),
     ("eulbfs_autotune", ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_float)]),
     ("eulbfs_set_tile", ct.c_int, [ct.c_void_p, ct.c_int]),
+    ("eulbfs_autotune_report", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int), ct.POINTER(ct.c_float), ct.c_int,
+                                          ct.POINTER(ct.c_int)]),
     ("eulbfs_diagnostics_noalloc", ct.c_int, [ct.c_int, ct.c_void_p, ct.c_int, ct.c_int, ct.POINTER(Props),
                                               ct.c_void_p, ct.c_void_p]),
     ("eulbfs_destroy", None, [ct.c_void_p]),
@@ -117,21 +119,39 @@ SIGNATURES = [
 ]
 
 
+# entry points of include/eulbfs_peaks.h (measured FMA throughput)
+PEAK_SIGNATURES = [
+    ("eulbfs_peak_fma", ct.c_int, [ct.c_int, ct.c_longlong, ct.c_void_p, ct.POINTER(ct.c_double),
+                                   ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]),
+]
+PEAK_FP32, PEAK_FP32X2, PEAK_FP64 = range(3)
+
+
 def lib():
-    """Load libeulbfs.so; raises if it has not been built."""
+    """Load libeulbfs.so; raises if it has not been built.  EULBFS_LIB names
+    another build of the same library (e.g. one compiled with other flags)."""
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(LIB_PATH):
-                raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; "
+            path = os.environ.get("EULBFS_LIB") or LIB_PATH
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with `python -c \"import __graft_entry__ as g; "
                                    f"g.build()\"` (there is no CPU fallback)")
-            L = ct.CDLL(LIB_PATH)
-            for name, res, args in SIGNATURES:
+            L = ct.CDLL(path)
+            for name, res, args in SIGNATURES + PEAK_SIGNATURES:
                 fn = getattr(L, name)
                 fn.restype = res
                 fn.argtypes = args
             _lib = L
     return _lib
+
+
+def peak_fma(kind: int, iters: int, stream: Optional[int] = None) -> dict:
+    """One timed launch of the FMA-chain kernel of `kind` (PEAK_*)."""
+    fl, ms, wi = ct.c_double(), ct.c_double(), ct.c_double()
+    _check(lib().eulbfs_peak_fma(kind, iters, ct.c_void_p(stream) if stream else None, ct.byref(fl), ct.byref(ms),
+                                 ct.byref(wi)))
+    return {"flops_per_s": fl.value, "ms": ms.value, "fma_warp_inst_per_s": wi.value}
 
 
 def _check(rc: int):
@@ -244,6 +264,12 @@ class Solver:
         rows, ms = ct.c_int(), ct.c_float()
         _check(lib().eulbfs_autotune(self._h, steps_per_candidate, ct.byref(rows), ct.byref(ms)))
         return rows.value, ms.value
+
+    def autotune_report(self) -> dict:
+        """{rows: best ms per step} of the candidates the last autotune timed."""
+        rows, ms, n = (ct.c_int * 8)(), (ct.c_float * 8)(), ct.c_int()
+        _check(lib().eulbfs_autotune_report(self._h, rows, ms, 8, ct.byref(n)))
+        return {rows[k]: ms[k] for k in range(min(n.value, 8))}
 
     def launches_per_step(self) -> int:
         return lib().eulbfs_launches_per_step(self._h)

@@ -75,12 +75,13 @@ class ServeReport:
 
 def serve(requests, precision: int = eulbfs.FP32C, budget_bytes: int = 0, chunk: int = 16,
           keep_fields: bool = False, stream: Optional[int] = None, realtime: bool = True,
-          clock=time.perf_counter) -> ServeReport:
+          clock=time.perf_counter, resident_cap: int = 0) -> ServeReport:
     """Serve `requests` (workloads.Request: rid, arrival_s, case, steps).
 
     realtime=True replays arrivals against the wall clock (arrival_s after the
     start); realtime=False admits every case as soon as it fits (a closed loop,
-    for tests).  A case whose state becomes non-finite is retired with that
+    for tests).  resident_cap > 0 caps the cases on the device at once (1:
+    one solve after another, no batching).  A case whose state becomes non-finite is retired with that
     error after the chunk in which it diverged and does not affect the others.
     A CUDA error from a launch is sticky for the whole context, so it retires
     every running case with that error."""
@@ -100,7 +101,8 @@ def serve(requests, precision: int = eulbfs.FP32C, budget_bytes: int = 0, chunk:
     try:
         while pending or running:
             # admit in arrival order while the budget allows
-            while pending and (not realtime or pending[0].arrival_s <= now()):
+            while pending and (not realtime or pending[0].arrival_s <= now()) and \
+                    (resident_cap <= 0 or len(running) < resident_cap):
                 r = pending[0]
                 need = lib.eulbfs_domain_bytes(r.case.nx, r.case.ny, precision)
                 if budget_bytes and need > budget_bytes:

@@ -14,8 +14,8 @@ from paper_2507_03366_gb300 import workloads as wl
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "eulbfs.h")).read()
+def _declared(header="eulbfs.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(eulbfs_[a-z_0-9]+)\s*\(", src)))
 
@@ -33,6 +33,16 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
     # the binding wraps exactly the declared entry points
     assert sorted(n for n, _, _ in eulbfs.SIGNATURES) == names
+
+
+def test_every_header_in_include_is_exported(lib):
+    """Every header under include/ declares entry points of libeulbfs.so."""
+    headers = sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+    assert "eulbfs_peaks.h" in headers
+    for h in headers:
+        for n in _declared(h):
+            assert hasattr(lib, n), (h, n)
+    assert sorted(n for n, _, _ in eulbfs.PEAK_SIGNATURES) == _declared("eulbfs_peaks.h")
 
 
 def test_version_and_sizes(lib):

@@ -1,10 +1,35 @@
 """Host-side arithmetic of bench.py that needs no GPU."""
 import bench
 
+PEAKS = {"fp32": {"tflops": 80.0, "fma_warp_inst_per_s": 1.25e12},
+         "fp32x2": {"tflops": 79.0, "fma_warp_inst_per_s": 0.62e12},
+         "fp64": {"tflops": 1.2, "fma_warp_inst_per_s": 1.8e10}}
 
-def test_binding_roof_follows_the_machine_balance():
-    # 80.5 TFLOP/s over 6.78 TB/s: the balance is 11.9 flop/B
-    assert bench.binding_roof(81.3, 939, 6777.3, 80.5) == "hbm"      # 11.5 flop/B
-    assert bench.binding_roof(81.3, 1142, 6777.3, 80.5) == "alu"     # 14.0 flop/B
-    assert bench.binding_roof(1.0, 0.0, 6777.3, 80.5) == "hbm"
-    assert bench.binding_roof(0.0, 1.0, 6777.3, 80.5) == "alu"
+
+def test_roofline_names_the_roof_with_the_largest_fraction(monkeypatch):
+    monkeypatch.setattr(bench, "counters_current", lambda: True)
+    cells = 6_795_264
+    r = bench.roofline(cells, "rz", 0.3806, 6680.5, PEAKS)
+    fr = {k: v["frac"] for k, v in r["roofs"].items()}
+    assert r["binding_roof"] == max(fr, key=fr.get)
+    assert r["frac"] == fr[r["binding_roof"]]
+    # compulsory bytes: 64 B per cell and step, a third per stage launch
+    comp = r["roofs"]["hbm_compulsory"]
+    assert abs(comp["achieved"] - 64 / 3 * cells / 0.3806e-3 / 1e9) < 1e-6
+    assert r["roofs"]["hbm_stage_by_stage"]["frac"] > comp["frac"]
+    # an issue-bound kernel: the issue roof binds and the bound is "alu"
+    assert r["binding_roof"] == "issue" and r["bound"] == "alu"
+    assert r["traffic"] == bench.COUNTERS["dram_bytes_per_cell_launch"]["rz"] * cells
+
+
+def test_stale_counters_are_not_reported(monkeypatch):
+    monkeypatch.setattr(bench, "counters_current", lambda: False)
+    r = bench.roofline(1_000_000, "xy", 0.05, 6680.5, PEAKS)
+    assert r["traffic"] is None and not r["counters_current"]
+    assert r["roofs"]["issue"]["achieved"] is None and r["roofs"]["fp32"]["frac"] is None
+    assert r["binding_roof"].startswith("hbm_")     # only the byte roofs remain
+
+
+def test_kernel_hash_covers_the_stage_kernel_sources():
+    h = bench.kernel_sources_sha256()
+    assert len(h) == 64 and bench.counters_current() == (h == bench.COUNTERS["sources_sha256"])
