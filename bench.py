@@ -49,11 +49,11 @@ BYTES_STAGE_BY_STAGE = {1: 244, 0: 352}
 # captured again.
 KERNEL_SOURCES = ("stage.cu", "device_common.cuh", "eulbfs_internal.h")
 COUNTERS = {
-    "sources_sha256": "4b42f2a81d586bd7cf82e5af8d2c4d717f6aeee91f3432563f568c1480f609ba",
-    "fp32_flops_per_cell_stage": {"rz": 939, "xy": 901},
-    "warp_inst_per_cell_stage": {"rz": 43.1, "xy": 41.7},
-    "dram_bytes_per_cell_launch": {"rz": 64.4, "xy": 64.4},
-    "fp64_flops_per_cell_stage": {"rz": 1035, "xy": 958},
+    "sources_sha256": "cc2b8d28459f14525b286ddb28541a6e6e614e8d68ce65aaab059b57ec648368",
+    "fp32_flops_per_cell_stage": {"rz": 946.0, "xy": 908.1},
+    "warp_inst_per_cell_stage": {"rz": 43.54, "xy": 42.14},
+    "dram_bytes_per_cell_launch": {"rz": 64.1, "xy": 64.2},
+    "fp64_flops_per_cell_stage": {"rz": 1023.6, "xy": 949.3},
 }
 # Streaming steps (dt_h, dt_f, dt_g) of the general-face-path leg.
 GEN_STEPS = (0.3, 0.4, 0.3)

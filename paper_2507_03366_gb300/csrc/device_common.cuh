@@ -72,21 +72,18 @@ __device__ __forceinline__ Q4<float> ld4(const Q4<float>& q) {
     return Q4<float>{v.x, v.y, v.z, v.w};
 }
 
-// With Eq. 7 as printed (K.lit): H_s = C_p,s T_s and H_l = C_p,l T_l + L with
-// the pure phases' heat capacities, and the solid branch's C_p is C_p,s (Eq. 7
-// at F_s = 1); the liquid branch's is Eq. 7 at F_s = 0 in both readings.
+// The branches' heat capacities and H_l come from constant groups, so both
+// readings run the same instructions: reading R1 mixes both heat capacities
+// by C~ and H_l = C_p^liq T_l + L; with Eq. 7 as printed H_s = C_p,s T_s and
+// H_l = C_p,l T_l + L with the pure phases' heat capacities, the solid
+// branch's C_p is C_p,s (Eq. 7 at F_s = 1) and the liquid branch's Eq. 7 at
+// F_s = 0 (as in R1).
 template <class R>
 __device__ __forceinline__ void invert_enthalpy(const Consts<R>& K, R Hh, R Hl, R Ct, R& T, R& Fl) {
-    const Q4<R> cp = ld4(K.mcp), e = ld4(K.enth);
-    const R cpl = fma(Ct, cp.w, cp.x);     // C~ cp_l + (1 - C~) cp_g
-    R cps, HL;
-    if (K.lit) {
-        cps = K.cp[0];
-        HL = fma(K.cp[1], e.y, e.z);
-    } else {
-        cps = fma(Ct, cp.y, cp.x);         // C~ cp_s + (1 - C~) cp_g
-        HL = fma(cpl, e.y, e.z);
-    }
+    const Q4<R> cp = ld4(K.enthc), e = ld4(K.enth);
+    const R cps = fma(Ct, cp.y, cp.x);     // R1: C~ cp_s + (1 - C~) cp_g
+    const R cpl = fma(Ct, cp.w, cp.z);     // C~ cp_l + (1 - C~) cp_g
+    const R HL = fma(cpl, K.hl[0], K.hl[1]);
     const R Hs = cps * e.x;
     const R ds = (Hh - Hs) + Hl;
     const R dl = (Hh - HL) + Hl;
@@ -105,21 +102,31 @@ __device__ __forceinline__ void invert_enthalpy(const Consts<R>& K, R Hh, R Hl, 
     }
 }
 
-// Eq. 7 (reading R1): gamma = C~ [F_s g_s + F_l g_l] + (1 - C~) g_g, as
-// g_g + C~ ((g_s - g_g) + F_l (g_l - g_s)) from the property's group.  As
-// printed (lit): F_s g_s + (1 - F_s)(C~ g_l + (1 - C~) g_g), as
-// m + F_s ((g_s - g_g) - C~ (g_l - g_g)) with m = g_g + C~ (g_l - g_g).
+// Eq. 7 as m.x + X (m.y + Y m.z).  Reading R1: gamma = C~ [F_s g_s + F_l g_l]
+// + (1 - C~) g_g = g_g + C~ ((g_s - g_g) + F_l (g_l - g_s)), (X, Y) = (C~, F_l).
+// As printed: F_s g_s + (1 - F_s)(C~ g_l + (1 - C~) g_g)
+// = g_s + F_l ((g_g - g_s) + C~ (g_l - g_g)), (X, Y) = (F_l, C~).  The weights
+// are swapped by the reading flag K.printed (0 or 1), without a branch.
 template <class R>
-__device__ __forceinline__ R mix(R Ct, R Fl, const Q4<R>& m, bool lit) {
-    if (lit) return fma(R(1) - Fl, fma(-Ct, m.w, m.y), fma(Ct, m.w, m.x));
-    return fma(Ct, fma(Fl, m.z, m.y), m.x);
+struct MixW { R X, Y; };
+
+template <class R>
+__device__ __forceinline__ MixW<R> mix_weights(const Consts<R>& K, R Ct, R Fl) {
+    const R p = K.printed;
+    const R d = Fl - Ct;
+    return MixW<R>{fma(p, d, Ct), fma(-p, d, Fl)};
+}
+
+template <class R>
+__device__ __forceinline__ R mix(const MixW<R>& w, const Q4<R>& m) {
+    return fma(w.X, fma(w.Y, m.z, m.y), m.x);
 }
 
 // The factor on F_s in the volume-change sources and the solid projection:
 // C~ (reading R1), 1 with Eq. 7 as printed.
 template <class R>
 __device__ __forceinline__ R solid_gate(const Consts<R>& K, R C) {
-    return K.lit ? R(1) : clamp01(C);
+    return fmax(clamp01(C), K.printed);
 }
 
 // Map a cell coordinate outside [0, n) through its boundary: periodic wrap or
@@ -207,11 +214,11 @@ __device__ __forceinline__ Prim<R> derive(const Consts<R>& K, const SV<R>& w) {
     const R C = w.Ch + w.Cl;
     const R Ct = clamp01(C);
     invert_enthalpy(K, w.Hh, w.Hl, Ct, q.T, q.Fl);
-    const bool lit = K.lit;
-    q.cp = mix(Ct, q.Fl, ld4(K.mcp), lit);
-    q.rho = mix(Ct, q.Fl, ld4(K.mrho), lit);
-    q.lam = mix(Ct, q.Fl, ld4(K.mlam), lit);
-    q.mu = mix(Ct, q.Fl, ld4(K.mmu), lit);
+    const MixW<R> mw = mix_weights(K, Ct, q.Fl);
+    q.cp = mix(mw, ld4(K.mcp));
+    q.rho = mix(mw, ld4(K.mrho));
+    q.lam = mix(mw, ld4(K.mlam));
+    q.mu = mix(mw, ld4(K.mmu));
     const R r3 = wdiv(R(3), q.rho);     // 1 / (rho cs^2)
     q.u = w.mx * r3;
     q.v = w.my * r3;

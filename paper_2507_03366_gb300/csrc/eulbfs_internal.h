@@ -54,11 +54,21 @@ struct alignas(16) Q4 { R x, y, z, w; };
 // on the device by the auxiliary kernels.
 template <class R>
 struct Consts {
-    // groups read with one load (Q4): Eq. 7 mixtures of C_p, rho, lambda, mu
-    // as {g_g, g_s - g_g, g_l - g_s, g_l - g_g}; {T_s, T_l, L, T_l - T_s};
-    // face {Q, C_ref / 6, 6 / C_ref, tau_g - 1/2}; cell {kv, g_x, g_y, 1 / dt}
-    // and {2 beta, kappa, dt, dt_f}
-    Q4<R> mcp, mrho, mlam, mmu, enth, facec, cellc, cellc2;
+    // groups read with one load (Q4):
+    //  - Eq. 7 mixtures of C_p, rho, lambda, mu: gamma = m.x + X (m.y + Y m.z)
+    //    with reading R1's {g_g, g_s - g_g, g_l - g_s} and (X, Y) = (C~, F_l),
+    //    or, with Eq. 7 as printed, {g_s, g_g - g_s, g_l - g_g} and
+    //    (X, Y) = (F_l, C~);
+    //  - {T_s, T_l, L, T_l - T_s};
+    //  - the heat capacities of Eq. 6's branches, C_p^sol = x + C~ y and
+    //    C_p^liq = z + C~ w: R1 {cp_g, cp_s - cp_g, cp_g, cp_l - cp_g}, as
+    //    printed {cp_s, 0, cp_g, cp_l - cp_g};
+    //  - face {Q, C_ref / 6, 6 / C_ref, tau_g - 1/2}; cell {kv, g_x, g_y, 1 / dt}
+    //    and {2 beta, kappa, dt, dt_f}
+    Q4<R> mcp, mrho, mlam, mmu, enth, enthc, facec, cellc, cellc2;
+    // H_l = C_p^liq hl[0] + hl[1]: R1 {T_l, L}, as printed {0, cp_l T_l + L}
+    alignas(2 * sizeof(R)) R hl[2];
+    R printed;                 // 1 with Eq. 5-7 as printed, 0 with reading R1
     R cp[3];                   // solid, liquid, gas (the forward closure of the initial state)
     R L, Ts, Tl;
     R dth, dtf, dtg;           // streaming steps of h, f, g
@@ -83,19 +93,27 @@ __host__ __device__ inline Q4<R> make_q4(double x, double y, double z, double w)
     return q;
 }
 
-// {g_g, g_s - g_g, g_l - g_s, g_l - g_g} of one property (solid, liquid, gas)
+// The Eq. 7 group of one property (solid, liquid, gas): reading R1
+// {g_g, g_s - g_g, g_l - g_s}, Eq. 7 as printed {g_s, g_g - g_s, g_l - g_g}.
 template <class R>
-__host__ __device__ inline Q4<R> mixture_q4(const double g[3]) {
-    return make_q4<R>(g[2], g[0] - g[2], g[1] - g[0], g[1] - g[2]);
+__host__ __device__ inline Q4<R> mixture_q4(const double g[3], bool printed) {
+    if (printed) return make_q4<R>(g[0], g[2] - g[0], g[1] - g[2], 0.0);
+    return make_q4<R>(g[2], g[0] - g[2], g[1] - g[0], 0.0);
 }
 
 template <class R>
 __host__ __device__ inline void fill_consts(const DomainDesc& d, Consts<R>& K) {
-    K.mcp = mixture_q4<R>(d.cp);
-    K.mrho = mixture_q4<R>(d.rho);
-    K.mlam = mixture_q4<R>(d.lam);
-    K.mmu = mixture_q4<R>(d.mu);
+    const bool printed = d.literal_eq7 != 0;
+    K.mcp = mixture_q4<R>(d.cp, printed);
+    K.mrho = mixture_q4<R>(d.rho, printed);
+    K.mlam = mixture_q4<R>(d.lam, printed);
+    K.mmu = mixture_q4<R>(d.mu, printed);
     K.enth = make_q4<R>(d.Ts, d.Tl, d.L, d.Tl - d.Ts);
+    K.enthc = printed ? make_q4<R>(d.cp[0], 0.0, d.cp[2], d.cp[1] - d.cp[2])
+                      : make_q4<R>(d.cp[2], d.cp[0] - d.cp[2], d.cp[2], d.cp[1] - d.cp[2]);
+    K.hl[0] = printed ? R(0) : (R)d.Tl;
+    K.hl[1] = printed ? (R)(d.cp[1] * d.Tl + d.L) : (R)d.L;
+    K.printed = printed ? R(1) : R(0);
     K.facec = make_q4<R>(d.Qg, d.Cref / 6.0, 6.0 / d.Cref, d.tau_g - 0.5);
     K.cellc = make_q4<R>(d.kv, d.gx, d.gy, 1.0 / d.dt);
     K.cellc2 = make_q4<R>(2.0 * d.beta, d.kappa, d.dt, d.dts[1]);

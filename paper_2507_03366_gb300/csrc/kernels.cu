@@ -47,7 +47,7 @@ __global__ void init_kernel(const DomainDesc* dd, const double* T, const double*
         const double H = enthalpy_of(Kd, T[c], Fl ? Fl[c] : 1.0, Cc);
         double Td, Fld;
         invert_enthalpy(Kd, H, 0.0, clamp01(Cc), Td, Fld);
-        const double rho = mix(clamp01(Cc), Fld, Kd.mrho, Kd.lit);
+        const double rho = mix(mix_weights(Kd, clamp01(Cc), Fld), Kd.mrho);
         SV<R> s;
         if (sizeof(R) == 8) { s.Hh = (R)H; s.Hl = 0; s.Ch = (R)Cc; s.Cl = 0; }
         else { put_pair(s.Hh, s.Hl, H); put_pair(s.Ch, s.Cl, Cc); }
@@ -75,7 +75,7 @@ __global__ void fields_kernel(const DomainDesc* dd, long long n, double* H, doub
         const double Hd = pair_value(w.Hh, w.Hl), Cd = pair_value(w.Ch, w.Cl);
         double Td, Fld;
         invert_enthalpy(Kd, Hd, 0.0, clamp01(Cd), Td, Fld);
-        const double rho = mix(clamp01(Cd), Fld, Kd.mrho, Kd.lit);
+        const double rho = mix(mix_weights(Kd, clamp01(Cd), Fld), Kd.mrho);
         if (H) H[c] = Hd;
         if (T) T[c] = Td;
         if (Fl) Fl[c] = Fld;
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kDiagThreads) diag_partial_kernel(const Domain
         const double H = pair_value(w.Hh, w.Hl), C = pair_value(w.Ch, w.Cl);
         double T, Fl;
         invert_enthalpy(Kd, H, 0.0, clamp01(C), T, Fl);
-        const double rho = mix(clamp01(C), Fl, Kd.mrho, Kd.lit);
+        const double rho = mix(mix_weights(Kd, clamp01(C), Fl), Kd.mrho);
         // cell volume: 1, or the radius r_i = i + 1/2 per radian (axisymmetric)
         const double vol = Kd.axi ? (double)(c % Kd.nx) + 0.5 : 1.0;
         acc[0] += vol * rho;
@@ -275,7 +275,7 @@ diag_partial_noalloc_kernel(Consts<double> Kd, const R* b, long long n, double* 
         const double H = pair_value(w.Hh, w.Hl), C = pair_value(w.Ch, w.Cl);
         double T, Fl;
         invert_enthalpy(Kd, H, 0.0, clamp01(C), T, Fl);
-        const double rho = mix(clamp01(C), Fl, Kd.mrho, Kd.lit);
+        const double rho = mix(mix_weights(Kd, clamp01(C), Fl), Kd.mrho);
         acc[0] += rho;
         acc[1] += H;
         acc[2] += C;
