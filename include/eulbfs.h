@@ -38,7 +38,8 @@ typedef enum {
     EULBFS_ENOMEM = 2,     /* device or host allocation failed */
     EULBFS_ECUDA = 3,      /* CUDA runtime error (no device, launch failure, ...) */
     EULBFS_ENONFINITE = 4, /* the state of some domain became NaN or Inf */
-    EULBFS_ETIMEOUT = 5,   /* a bounded device wait gave up (reserved) */
+    EULBFS_ETIMEOUT = 5,   /* a bounded device wait gave up (the stage kernel waits about a second
+                            * for each input tile it copies by TMA, then stops and reports this) */
     EULBFS_EBUSY = 6       /* a domain does not fit in the solver's memory budget */
 } eulbfs_status;
 
@@ -194,6 +195,23 @@ unsigned long long eulbfs_domain_bytes(int nx, int ny, int precision);
  * Errors: EINVAL, EBUSY (memory budget), ENOMEM, ECUDA. */
 int eulbfs_add_domain(eulbfs_solver* s, const eulbfs_domain* d, long long max_steps, int* slot);
 
+/* Add one domain split along y into k slabs that advance as k domains of
+ * this solver (the paper has no counterpart: it is the decomposition a
+ * domain spread over several devices needs, here within one device).  Slab i
+ * holds rows [i ny / k, (i + 1) ny / k) (integer division), at least 8 rows
+ * each, and 3 halo rows on each side it shares with a neighbour (both sides
+ * if y is periodic): the ghost width of the stencil (two rows for the
+ * gradients, a third for the Laplacian of C in mu_c).  After every
+ * Runge-Kutta stage the solver copies each slab's 3 outermost interior rows
+ * into its neighbours' halo rows, so every slab sees the rows the undivided
+ * domain would; results are bit for bit those of the undivided domain.
+ * slots: caller array of k slot indices (bottom slab first); each slab is
+ * read back (fields, state, diagnostics) as a domain of ny_i rows.  Remove
+ * the slabs of a split domain together.  k = 1 adds the domain whole.
+ * Errors: EINVAL (k < 1, ny < 8 k, or the domain's own errors), EBUSY,
+ * ENOMEM, ECUDA. */
+int eulbfs_add_split_domain(eulbfs_solver* s, const eulbfs_domain* d, int k, long long max_steps, int* slots);
+
 /* Remove a domain and release its memory; its slot index is not reused. */
 int eulbfs_remove_domain(eulbfs_solver* s, int slot);
 
@@ -214,7 +232,9 @@ int eulbfs_domain_progress(const eulbfs_solver* s, int slot, long long* done, lo
 int eulbfs_step(eulbfs_solver* s, long long n);
 
 /* Wait for the solver's stream.  Returns ENONFINITE if a stage of any
- * domain produced a NaN or Inf since the solver was created. */
+ * domain produced a NaN or Inf since the solver was created, ETIMEOUT if a
+ * stage kernel gave up waiting for an input tile (its results are then not
+ * valid). */
 int eulbfs_sync(eulbfs_solver* s);
 
 /* Slots of the live domains whose own state became NaN or Inf (their
@@ -264,7 +284,9 @@ int eulbfs_load(eulbfs_solver* s, int slot, const void* buf, unsigned long long 
  * total mass, enthalpy and largest speed. */
 int eulbfs_diagnostics(eulbfs_solver* s, int slot, eulbfs_diag* d);
 
-/* Number of kernels the solver launches per time step of the current batch. */
+/* Number of kernels the solver launches per time step of the current batch:
+ * three stage launches, and a halo copy after each while a split domain's
+ * slabs are active. */
 int eulbfs_launches_per_step(const eulbfs_solver* s);
 
 /* Capture eulbfs_step's per-step launches in a CUDA graph of `steps_per_graph`
@@ -317,6 +339,16 @@ int eulbfs_diagnostics_noalloc(int precision, const void* state, int nx, int ny,
  * stream.  EULBFS_EINVAL for a null solver or steps_per_candidate < 1; a
  * failing step returns its error and leaves the height unchanged. */
 int eulbfs_autotune(eulbfs_solver* s, int steps_per_candidate, int* best_rows, float* best_ms_per_step);
+
+/* Test hook for the bounded device waits (no counterpart in the paper).
+ * With on = 1 every input-tile barrier of the stage kernel expects 16 bytes
+ * more than its copy delivers, so every tile wait runs out after its bound
+ * (about a second of SM clocks, twice: the wait and the wait for the copy in
+ * flight) and the kernel stops; eulbfs_sync then returns ETIMEOUT and the
+ * CUDA context stays usable.  on = 0 (the default) restores normal waits.
+ * Only domains whose state buffers get tensor maps (nx a multiple of 4 in
+ * FP32C) and interior work items wait on tiles.  Errors: EINVAL. */
+int eulbfs_set_tile_wait_probe(eulbfs_solver* s, int on);
 
 /* The candidates the last eulbfs_autotune of this solver timed: up to `cap`
  * heights (rows) and their best milliseconds per step; *n receives how many

@@ -8,6 +8,7 @@
 // from a captured CUDA graph; each stage launch and each graph replay is an
 // NVTX range for profilers.  Domains can be added and removed between steps
 // (continuous batching) under a device-memory budget.
+#include <cuda.h>           // CUtensorMap and its enums only: the encoder is fetched through the runtime
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>   // header-only: ranges cost a pointer test unless a profiler is attached
 
@@ -43,6 +44,7 @@ int cuda_fail(cudaError_t e, const char* what) {
     } while (0)
 
 constexpr double kDtStream = 0.5;   // c dt_s = dx / 2 (Sec. 2.5 step (1))
+constexpr int kMinSlabRows = 8;     // interior rows of each slab of a split domain
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -102,12 +104,17 @@ int validate(const eulbfs_grid& g, const eulbfs_props& P, const eulbfs_bc& B, co
     return EULBFS_OK;
 }
 
-DomainDesc make_desc(const eulbfs_grid& g, const eulbfs_props& P, const eulbfs_bc& B, const eulbfs_numerics& N) {
+// hlo, hhi: halo rows below / above a slab of a split domain (0 otherwise).
+DomainDesc make_desc(const eulbfs_grid& g, const eulbfs_props& P, const eulbfs_bc& B, const eulbfs_numerics& N,
+                     int hlo = 0, int hhi = 0) {
     DomainDesc d{};
     d.nx = g.nx;
     d.ny = g.ny;
+    d.hlo = hlo;
+    d.hhi = hhi;
     d.per_x = B.xlo.thermal == EULBFS_BC_PERIODIC;
-    d.per_y = B.ylo.thermal == EULBFS_BC_PERIODIC;
+    // a slab with halos reaches its neighbours through them, not by wrapping
+    d.per_y = B.ylo.thermal == EULBFS_BC_PERIODIC && !hlo && !hhi;
     const eulbfs_side* sides[4] = {&B.xlo, &B.xhi, &B.ylo, &B.yhi};
     for (int k = 0; k < 4; ++k) {
         d.bc_t[k] = sides[k]->thermal;
@@ -144,10 +151,12 @@ DomainDesc make_desc(const eulbfs_grid& g, const eulbfs_props& P, const eulbfs_b
     d.gx = P.gx;
     d.gy = P.gy;
     d.dt = N.dt;
-    d.plane = (long long)g.nx * g.ny;
+    d.plane = (long long)g.nx * (g.ny + hlo + hhi);
+    d.off = (long long)hlo * g.nx;
     return d;
 }
 
+// Bytes of one domain's allocation; n = elements per plane (halo rows included).
 size_t domain_bytes(long long n, int precision) {
     const size_t e = elem_of(precision);
     return align256(sizeof(DomainDesc)) + 256 /* flag */ + 3 * align256((size_t)planes_of(precision) * n * e) +
@@ -165,6 +174,8 @@ struct eulbfs_solver {
     std::vector<Dom> doms;
     void* d_consts = nullptr;      // Consts<R>[ndomains] in the working precision
     size_t consts_cap = 0;
+    void* d_tmaps = nullptr;       // CUtensorMap[ndomains][3] of the state buffers
+    size_t tmaps_cap = 0;
     int4* d_items = nullptr;       // work items (domain, strip, segment, 0)
     int items_cap = 0;
     int nitems = 0;
@@ -189,6 +200,15 @@ struct eulbfs_solver {
     int tune_n = 0;
     int tune_rows[8] = {};
     float tune_ms[8] = {};
+    unsigned tile_probe = 0;       // eulbfs_set_tile_wait_probe
+    // split domains: (lower slab, upper slab) pairs whose halo rows are
+    // exchanged after every stage; the active ones on the device
+    std::vector<int2> links;
+    int2* d_links = nullptr;
+    int links_cap = 0;
+    int nlinks = 0;                // active links uploaded
+    int link_nx = 0;               // widest linked slab
+    bool halo_stale = false;       // W^n was written outside a stage: refresh its halos before stepping
 };
 
 namespace {
@@ -199,12 +219,55 @@ void drop_graph(eulbfs_solver* s) {
     s->graph_valid = false;
 }
 
+static_assert(sizeof(CUtensorMap) == kTmapBytes, "tensor map size");
+
+typedef CUresult (*encode_tiled_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry points (no link
+// against the driver library); null if the driver does not provide it.
+encode_tiled_fn tensor_map_encoder() {
+    static encode_tiled_fn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<encode_tiled_fn>(f);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor map of one state buffer: columns x rows x planes, box kTileX x
+// kChunk x all planes.  A TMA copy needs 16-byte aligned rows and planes, so
+// domains whose row (nx elements) is not a multiple of 16 bytes get none and
+// the stage kernel loads their cells directly.
+bool encode_state_map(CUtensorMap* m, void* base, int precision, int nx, long long rows, long long plane) {
+    encode_tiled_fn enc = tensor_map_encoder();
+    const size_t e = elem_of(precision);
+    if (!enc || (nx * e) % 16 != 0 || (plane * e) % 16 != 0 || reinterpret_cast<uintptr_t>(base) % 16 != 0)
+        return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)rows, (cuuint64_t)planes_of(precision)};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * e, (cuuint64_t)plane * e};
+    const cuuint32_t box[3] = {(cuuint32_t)kTileX, (cuuint32_t)kChunk, (cuuint32_t)planes_of(precision)};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(m, precision == EULBFS_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                           3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 template <class R>
-std::vector<unsigned char> consts_image(const std::vector<Dom>& doms) {
+std::vector<unsigned char> consts_image(const std::vector<Dom>& doms, const std::vector<char>& tma) {
     std::vector<unsigned char> img(sizeof(Consts<R>) * doms.size());
     for (size_t k = 0; k < doms.size(); ++k) {
         Consts<R> K{};
         fill_consts(doms[k].desc, K);
+        K.tma = tma[k];
         std::memcpy(img.data() + k * sizeof(Consts<R>), &K, sizeof(K));
     }
     return img;
@@ -214,8 +277,28 @@ std::vector<unsigned char> consts_image(const std::vector<Dom>& doms) {
 // per-domain constants after the set of domains or the segment height changed.
 int rebuild(eulbfs_solver* s) {
     const int nd = (int)s->doms.size();
+    // tensor maps of every live domain's three state buffers
+    std::vector<CUtensorMap> maps((size_t)nd * 3);
+    std::vector<char> tma(nd, 0);
+    for (int k = 0; k < nd; ++k) {
+        const Dom& d = s->doms[k];
+        if (!d.alive) continue;
+        bool ok = true;
+        for (int b = 0; b < 3 && ok; ++b)
+            ok = encode_state_map(&maps[(size_t)k * 3 + b], d.desc.st[b], s->precision, d.grid.nx,
+                                  (long long)d.grid.ny + d.desc.hlo + d.desc.hhi, d.desc.plane);
+        tma[k] = ok ? 1 : 0;
+    }
     std::vector<unsigned char> img =
-        s->precision == EULBFS_FP64 ? consts_image<double>(s->doms) : consts_image<float>(s->doms);
+        s->precision == EULBFS_FP64 ? consts_image<double>(s->doms, tma) : consts_image<float>(s->doms, tma);
+    const size_t map_bytes = sizeof(CUtensorMap) * maps.size();
+    if (map_bytes > s->tmaps_cap) {
+        if (s->d_tmaps) cudaFree(s->d_tmaps);
+        s->d_tmaps = nullptr;
+        s->tmaps_cap = std::max(map_bytes, 2 * s->tmaps_cap);
+        CK(cudaMalloc(&s->d_tmaps, s->tmaps_cap), "tensor maps");
+    }
+    if (map_bytes) CK(cudaMemcpyAsync(s->d_tmaps, maps.data(), map_bytes, cudaMemcpyHostToDevice, s->stream), "upload tensor maps");
     if (img.size() > s->consts_cap) {
         if (s->d_consts) cudaFree(s->d_consts);
         s->consts_cap = std::max(img.size(), 2 * s->consts_cap);
@@ -238,6 +321,22 @@ int rebuild(eulbfs_solver* s) {
         CK(cudaMalloc(&s->d_items, sizeof(int4) * s->items_cap), "work list");
     }
     if (s->nitems) CK(cudaMemcpyAsync(s->d_items, items.data(), sizeof(int4) * s->nitems, cudaMemcpyHostToDevice, s->stream), "upload work list");
+    // halo links between active slabs
+    std::vector<int2> act;
+    s->link_nx = 0;
+    for (const int2& l : s->links)
+        if (l.x < nd && l.y < nd && s->doms[l.x].active() && s->doms[l.y].active()) {
+            act.push_back(l);
+            s->link_nx = std::max(s->link_nx, s->doms[l.x].grid.nx);
+        }
+    s->nlinks = (int)act.size();
+    if (s->nlinks > s->links_cap) {
+        if (s->d_links) cudaFree(s->d_links);
+        s->d_links = nullptr;
+        s->links_cap = std::max(s->nlinks, 2 * s->links_cap);
+        CK(cudaMalloc(&s->d_links, sizeof(int2) * s->links_cap), "halo links");
+    }
+    if (s->nlinks) CK(cudaMemcpyAsync(s->d_links, act.data(), sizeof(int2) * s->nlinks, cudaMemcpyHostToDevice, s->stream), "upload links");
     // the host vectors die here: make the copies complete before returning
     CK(cudaStreamSynchronize(s->stream), "rebuild sync");
     const int per_sm = stage_blocks_per_sm(s->precision);
@@ -250,6 +349,8 @@ int rebuild(eulbfs_solver* s) {
 int launch_step_direct(eulbfs_solver* s) {
     StageLaunch a;
     a.consts = s->d_consts;
+    a.tmaps = s->d_tmaps;
+    a.tile_probe = s->tile_probe;
     a.items = s->d_items;
     a.nitems = s->nitems;
     a.seg = s->seg;
@@ -259,6 +360,9 @@ int launch_step_direct(eulbfs_solver* s) {
         a.stage = st;
         nvtxRangePushA(kStageRange[st]);
         cudaError_t e = launch_stage(s->precision, a, s->grid, s->stream);
+        // split domains: the stage's output halos from the neighbouring slabs
+        if (e == cudaSuccess && s->nlinks)
+            e = launch_halo(s->precision, s->d_consts, s->d_links, s->nlinks, s->link_nx, st == 2 ? 0 : st + 1, s->stream);
         nvtxRangePop();
         if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
     }
@@ -306,13 +410,14 @@ int check_slot(const eulbfs_solver* s, int slot) {
     return EULBFS_OK;
 }
 
-int add_domain(eulbfs_solver* s, const eulbfs_domain& dm, long long max_steps, int* slot) {
+int add_domain(eulbfs_solver* s, const eulbfs_domain& dm, long long max_steps, int* slot, int hlo = 0, int hhi = 0) {
     int rc = validate(dm.grid, dm.props, dm.bc, dm.num);
     if (rc) return rc;
     if (!dm.init.T || !dm.init.C) return fail(EULBFS_EINVAL, "initial T and C are required");
     if (max_steps < 0) return fail(EULBFS_EINVAL, "max_steps must be >= 0");
-    const long long n = (long long)dm.grid.nx * dm.grid.ny;
-    const size_t bytes = domain_bytes(n, s->precision);
+    const long long n = (long long)dm.grid.nx * dm.grid.ny;                  // interior cells
+    const long long np = (long long)dm.grid.nx * (dm.grid.ny + hlo + hhi);   // elements per plane
+    const size_t bytes = domain_bytes(np, s->precision);
     if (s->budget && s->used + bytes > s->budget)
         return fail(EULBFS_EBUSY, "domain does not fit in the memory budget");
     Dom d;
@@ -321,7 +426,7 @@ int add_domain(eulbfs_solver* s, const eulbfs_domain& dm, long long max_steps, i
     d.bc = dm.bc;
     d.num = dm.num;
     d.max_steps = max_steps;
-    d.desc = make_desc(dm.grid, dm.props, dm.bc, dm.num);
+    d.desc = make_desc(dm.grid, dm.props, dm.bc, dm.num, hlo, hhi);
     if (cudaMalloc(&d.mem, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(EULBFS_ENOMEM, "device allocation of a domain failed");
@@ -335,10 +440,10 @@ int add_domain(eulbfs_solver* s, const eulbfs_domain& dm, long long max_steps, i
     const size_t e = elem_of(s->precision);
     for (int k = 0; k < 3; ++k) {
         d.desc.st[k] = p;
-        p += align256((size_t)planes_of(s->precision) * n * e);
+        p += align256((size_t)planes_of(s->precision) * np * e);
     }
     d.desc.Fsp = p;
-    p += align256(n * e);
+    p += align256(np * e);
     d.desc.dFs = p;
     CK(cudaMemsetAsync(d.mem, 0, bytes, s->stream), "clear domain");
     CK(cudaMemcpyAsync(d.d_desc, &d.desc, sizeof(DomainDesc), cudaMemcpyHostToDevice, s->stream), "upload descriptor");
@@ -377,6 +482,7 @@ int add_domain(eulbfs_solver* s, const eulbfs_domain& dm, long long max_steps, i
     s->doms.push_back(d);
     if (slot) *slot = (int)s->doms.size() - 1;
     s->dirty = true;
+    if (hlo || hhi) s->halo_stale = true;
     return EULBFS_OK;
 }
 
@@ -574,6 +680,13 @@ int eulbfs_autotune_report(const eulbfs_solver* s, int* rows, float* ms_per_step
     return EULBFS_OK;
 }
 
+int eulbfs_set_tile_wait_probe(eulbfs_solver* s, int on) {
+    if (!s || (on != 0 && on != 1)) return fail(EULBFS_EINVAL, "null solver or on not 0/1");
+    s->tile_probe = on ? 16u : 0u;
+    drop_graph(s);
+    return EULBFS_OK;
+}
+
 int eulbfs_use_graphs(eulbfs_solver* s, int steps_per_graph) {
     if (!s) return fail(EULBFS_EINVAL, "null solver");
     if (steps_per_graph < 0) return fail(EULBFS_EINVAL, "steps_per_graph must be >= 0");
@@ -582,7 +695,46 @@ int eulbfs_use_graphs(eulbfs_solver* s, int steps_per_graph) {
     return EULBFS_OK;
 }
 
-int eulbfs_launches_per_step(const eulbfs_solver* s) { return s ? 3 : 0; }
+int eulbfs_launches_per_step(const eulbfs_solver* s) {
+    if (!s) return 0;
+    const int nd = (int)s->doms.size();
+    for (const int2& l : s->links)   // a halo copy after each stage while two linked slabs are active
+        if (l.x < nd && l.y < nd && s->doms[l.x].active() && s->doms[l.y].active()) return 6;
+    return 3;
+}
+
+int eulbfs_add_split_domain(eulbfs_solver* s, const eulbfs_domain* d, int k, long long max_steps, int* slots) {
+    if (!s || !d || !slots) return fail(EULBFS_EINVAL, "null argument");
+    if (k < 1) return fail(EULBFS_EINVAL, "k must be >= 1");
+    if (k == 1) return add_domain(s, *d, max_steps, slots);
+    const int ny = d->grid.ny, nx = d->grid.nx;
+    if (ny < k * kMinSlabRows) return fail(EULBFS_EINVAL, "each slab needs at least 8 rows (ny >= 8 k)");
+    const bool per_y = d->bc.ylo.thermal == EULBFS_BC_PERIODIC;
+    const int first = (int)s->doms.size();
+    for (int i = 0; i < k; ++i) {
+        const int y0 = (int)((long long)i * ny / k), y1 = (int)((long long)(i + 1) * ny / k);
+        eulbfs_domain sl = *d;
+        sl.grid.ny = y1 - y0;
+        const long long o = (long long)y0 * nx;
+        const double* const* src[6] = {&d->init.T, &d->init.Fl, &d->init.C, &d->init.u, &d->init.v, &d->init.p};
+        const double** dst[6] = {&sl.init.T, &sl.init.Fl, &sl.init.C, &sl.init.u, &sl.init.v, &sl.init.p};
+        for (int f = 0; f < 6; ++f) *dst[f] = *src[f] ? *src[f] + o : nullptr;
+        const int hlo = (i > 0 || per_y) ? kHalo : 0, hhi = (i < k - 1 || per_y) ? kHalo : 0;
+        int slot = -1;
+        const int rc = add_domain(s, sl, max_steps, &slot, hlo, hhi);
+        if (rc) {
+            const std::string msg = eulbfs_last_error();
+            for (int j = first; j < (int)s->doms.size(); ++j) eulbfs_remove_domain(s, j);
+            return fail(rc, msg);
+        }
+        slots[i] = slot;
+    }
+    for (int i = 0; i + 1 < k; ++i) s->links.push_back(make_int2(slots[i], slots[i + 1]));
+    if (per_y) s->links.push_back(make_int2(slots[k - 1], slots[0]));
+    s->dirty = true;
+    s->halo_stale = true;
+    return EULBFS_OK;
+}
 
 int eulbfs_step(eulbfs_solver* s, long long n) {
     if (!s) return fail(EULBFS_EINVAL, "null solver");
@@ -593,6 +745,11 @@ int eulbfs_step(eulbfs_solver* s, long long n) {
             if (rc) return rc;
         }
         if (s->nitems == 0) break;
+        if (s->halo_stale) {   // W^n written by creation, set_state or load: its halos first
+            if (s->nlinks)
+                CK(launch_halo(s->precision, s->d_consts, s->d_links, s->nlinks, s->link_nx, 0, s->stream), "halo rows");
+            s->halo_stale = false;
+        }
         long long k = n;
         for (const Dom& d : s->doms)
             if (d.active() && d.max_steps > 0) k = std::min(k, d.max_steps - d.done);
@@ -625,6 +782,7 @@ int eulbfs_sync(eulbfs_solver* s) {
     if (!s) return fail(EULBFS_EINVAL, "null solver");
     CK(cudaMemcpyAsync(s->h_flag, s->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "flag copy");
     CK(cudaStreamSynchronize(s->stream), "stream sync");
+    if (*s->h_flag & 2) return fail(EULBFS_ETIMEOUT, "a bounded device wait for an input tile gave up");
     if (*s->h_flag & 1) return fail(EULBFS_ENONFINITE, "a non-finite state value was produced");
     return EULBFS_OK;
 }
@@ -660,7 +818,7 @@ int eulbfs_fields(eulbfs_solver* s, int slot, const eulbfs_fields_out* out) {
     if (rc) return rc;
     if (!out) return fail(EULBFS_EINVAL, "null output");
     const Dom& d = s->doms[slot];
-    const long long n = d.desc.plane;
+    const long long n = (long long)d.grid.nx * d.grid.ny;   // interior cells
     double* host[7] = {out->H, out->T, out->Fl, out->C, out->p, out->u, out->v};
     double* buf = nullptr;
     CK(cudaMalloc(&buf, sizeof(double) * n * 7), "fields scratch");
@@ -683,7 +841,7 @@ int eulbfs_get_state(eulbfs_solver* s, int slot, double* H, double* p, double* m
     int rc = check_slot(s, slot);
     if (rc) return rc;
     const Dom& d = s->doms[slot];
-    const long long n = d.desc.plane;
+    const long long n = (long long)d.grid.nx * d.grid.ny;   // interior cells
     double* host[6] = {H, p, mx, my, C, Fs_prev};
     double* buf = nullptr;
     CK(cudaMalloc(&buf, sizeof(double) * n * 6), "state scratch");
@@ -707,7 +865,7 @@ int eulbfs_set_state(eulbfs_solver* s, int slot, const double* H, const double* 
     (void)t;
     if (step < 0) return fail(EULBFS_EINVAL, "step must be >= 0");
     Dom& d = s->doms[slot];
-    const long long n = d.desc.plane;
+    const long long n = (long long)d.grid.nx * d.grid.ny;   // interior cells
     const double* host[6] = {H, p, mx, my, C, Fs_prev};
     double* buf = nullptr;
     CK(cudaMalloc(&buf, sizeof(double) * n * 6), "state scratch");
@@ -722,6 +880,7 @@ int eulbfs_set_state(eulbfs_solver* s, int slot, const double* H, const double* 
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     cudaFree(buf);
     if (e != cudaSuccess) return cuda_fail(e, "set_state");
+    s->halo_stale = true;
     d.done = step;
     if (d.finished()) s->dirty = true;
     return EULBFS_OK;
@@ -760,6 +919,7 @@ int eulbfs_load(eulbfs_solver* s, int slot, const void* buf, unsigned long long 
     CK(cudaMemcpyAsync(d.desc.st[0], h, st, cudaMemcpyHostToDevice, s->stream), "load state");
     CK(cudaMemcpyAsync(d.desc.Fsp, h + st, fs, cudaMemcpyHostToDevice, s->stream), "load F_s");
     CK(cudaStreamSynchronize(s->stream), "load sync");
+    s->halo_stale = true;
     d.done = step;
     if (d.finished()) s->dirty = true;
     return EULBFS_OK;
@@ -770,7 +930,7 @@ int eulbfs_diagnostics(eulbfs_solver* s, int slot, eulbfs_diag* out) {
     if (rc) return rc;
     if (!out) return fail(EULBFS_EINVAL, "null output");
     const Dom& d = s->doms[slot];
-    const long long n = d.desc.plane;
+    const long long n = (long long)d.grid.nx * d.grid.ny;   // interior cells
     const int nb = diag_blocks(n);
     if (nb > s->partial_cap) {
         CK(cudaStreamSynchronize(s->stream), "sync");
@@ -810,6 +970,8 @@ void eulbfs_destroy(eulbfs_solver* s) {
     for (Dom& d : s->doms)
         if (d.mem) cudaFree(d.mem);
     if (s->d_consts) cudaFree(s->d_consts);
+    if (s->d_tmaps) cudaFree(s->d_tmaps);
+    if (s->d_links) cudaFree(s->d_links);
     if (s->d_items) cudaFree(s->d_items);
     if (s->d_flag) cudaFree(s->d_flag);
     if (s->h_flag) cudaFreeHost(s->h_flag);

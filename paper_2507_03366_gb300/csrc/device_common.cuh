@@ -141,6 +141,16 @@ __device__ __forceinline__ void map_axis(int g, int n, int per, int lo_side, int
     s = s < 0 ? 0 : (s >= n ? n - 1 : s);   // layers deeper than the domain are never used
 }
 
+// map_axis along y for a slab of a split domain: rows within the halo
+// ([-hlo, 0) and [ny, ny + hhi)) are read where they are, with no boundary
+// rule (k = 0); rows beyond the halo are never used and are clamped into it.
+template <class R>
+__device__ __forceinline__ void map_row(const Consts<R>& K, int g, int& s, int& k, int& side) {
+    if (g < 0 && K.hlo) { s = g < -K.hlo ? -K.hlo : g; k = 0; side = YLO; return; }
+    if (g >= K.ny && K.hhi) { s = g > K.ny + K.hhi - 1 ? K.ny + K.hhi - 1 : g; k = 0; side = YHI; return; }
+    map_axis(g, K.ny, K.per_y, YLO, s, k, side);
+}
+
 // Ghost value rules (boundary conditions on macroscopic variables).
 template <class R>
 struct Prim { R T, Fl, cp, rho, lam, mu, p, u, v, C; };
@@ -165,20 +175,23 @@ __device__ __forceinline__ R wall_wetting(const Consts<R>& K, const R* in, int s
     const bool xs = side < 2;
     const int n = xs ? K.ny : K.nx, m = xs ? K.nx : K.ny;
     const int per = xs ? K.per_y : K.per_x;
+    // along a slab's halo rows the wall continues: the tangential range of an
+    // x side reaches into the halo
+    const int tlo = xs ? -K.hlo : 0, thi = xs ? n - 1 + K.hhi : n - 1;
     int tc, tp, tm;
     if (per) {
         tc = ((t % n) + n) % n;
         tp = tc + 1 == n ? 0 : tc + 1;
         tm = tc == 0 ? n - 1 : tc - 1;
     } else {
-        tc = t < 0 ? 0 : (t > n - 1 ? n - 1 : t);
-        tp = tc + 1 > n - 1 ? n - 1 : tc + 1;
-        tm = tc - 1 < 0 ? 0 : tc - 1;
+        tc = t < tlo ? tlo : (t > thi ? thi : t);
+        tp = tc + 1 > thi ? thi : tc + 1;
+        tm = tc - 1 < tlo ? tlo : tc - 1;
     }
     const int l0 = (side == XLO || side == YLO) ? 0 : m - 1;
     const int l1 = (side == XLO || side == YLO) ? 1 : m - 2;
     auto at = [&](int layer, int tt) -> R {
-        const long long c = xs ? (long long)tt * K.nx + layer : (long long)layer * K.nx + tt;
+        const long long c = (xs ? (long long)tt * K.nx + layer : (long long)layer * K.nx + tt) + K.off;
         return load_C(in, K.plane, c);
     };
     const R c0 = at(l0, tc);

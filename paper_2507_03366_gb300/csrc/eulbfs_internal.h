@@ -22,6 +22,10 @@ struct DomainDesc {
     int zero_solid_velocity;
     int axi;                 // 1: axisymmetric (r, z), x = r with the axis at x = 0
     int literal_eq7;         // 1: Eq. 5-7 as printed instead of reading R1
+    // A slab of a domain split along y: its planes hold hlo halo rows below
+    // and hhi above its ny interior rows (0 or kHalo each); halo rows are
+    // copies of the neighbouring slab's rows, not boundary ghosts.
+    int hlo, hhi;
     double Tw[4];            // wall temperature per side (Dirichlet)
     double wet[4];           // 4 cos(theta) / xi per side (wetting)
     double cos_adv[4], cos_rec[4];   // hysteresis window per side (WETTING_HYST)
@@ -41,7 +45,8 @@ struct DomainDesc {
     void* Fsp;               // F_s of the previous step
     void* dFs;               // (F_s^n - F_s^{n-1}) / dt of the current step
     int* flag;               // bit 0: this domain produced a non-finite state
-    long long plane;         // nx * ny
+    long long plane;         // nx * (ny + hlo + hhi): elements per plane
+    long long off;           // hlo * nx: plane index of interior cell (0, 0)
 };
 
 // Four constants that the kernels read together: one 16-byte shared-memory
@@ -78,6 +83,10 @@ struct Consts {
     int nx, ny, per_x, per_y, zsv, axi;
     int gen;                   // 1: some streaming step differs from 0.5 (general face path)
     int lit;                   // 1: Eq. 5-7 as printed instead of reading R1
+    int tma;                   // 1: the state buffers have tensor maps (stage kernel tiles by TMA)
+    int pad_;
+    int hlo, hhi;              // halo rows below / above (a slab of a split domain)
+    long long off;             // plane index of interior cell (0, 0)
     int bc_t[4], bc_f[4], bc_c[4];
     long long plane;
     void* st[3];
@@ -125,6 +134,8 @@ __host__ __device__ inline void fill_consts(const DomainDesc& d, Consts<R>& K) {
     K.tf_coef = (R)(3.0 / d.dts[1]);
     K.gen = (d.dts[0] != 0.5 || d.dts[1] != 0.5 || d.dts[2] != 0.5) ? 1 : 0;
     K.lit = d.literal_eq7;
+    K.tma = 0;                 // set by the host where the tensor maps exist
+    K.pad_ = 0;
     for (int k = 0; k < 4; ++k) {
         K.Tw[k] = (R)d.Tw[k]; K.wet[k] = (R)d.wet[k];
         K.cos_adv[k] = (R)d.cos_adv[k]; K.cos_rec[k] = (R)d.cos_rec[k];
@@ -133,6 +144,9 @@ __host__ __device__ inline void fill_consts(const DomainDesc& d, Consts<R>& K) {
     K.nx = d.nx; K.ny = d.ny; K.per_x = d.per_x; K.per_y = d.per_y;
     K.zsv = d.zero_solid_velocity; K.axi = d.axi;
     K.plane = d.plane;
+    K.hlo = d.hlo;
+    K.hhi = d.hhi;
+    K.off = d.off;
     for (int k = 0; k < 3; ++k) K.st[k] = d.st[k];
     K.Fsp = d.Fsp;
     K.dFs = d.dFs;
@@ -146,13 +160,22 @@ constexpr int kStripX = 31;   // 31 cells -> 32 x-faces per row: one per lane
 constexpr int kChunk = 8;
 constexpr int kStageThreads = 32 * kChunk;
 
+// The stage kernel's input tiles: kChunk rows x kTileX columns x all state
+// planes of one buffer, copied into shared memory by a TMA tensor copy.  The
+// first column is rounded down to a 16-byte boundary, so kTileX covers the
+// strip, its halo and up to three columns of offset.
+constexpr int kTileX = 40;
+constexpr int kTmapBytes = 128;   // sizeof(CUtensorMap)
+
 struct StageLaunch {
     const void* consts;      // Consts<R>[ndomains] in device memory
+    const void* tmaps;       // CUtensorMap[ndomains][3]: one per state buffer (used where Consts::tma)
     const int4* items;       // (domain, strip, segment, 0)
     int nitems;
     int stage;               // 0, 1, 2
     int seg;                 // segment height in rows (multiple of kChunk)
-    int* flag;               // bit 0: non-finite state seen
+    int* flag;               // bit 0: non-finite state seen; bit 1: a bounded wait for a tile gave up
+    unsigned tile_probe;     // bytes each tile barrier expects beyond its copy (0; > 0 only to test the bounded waits)
 };
 
 // Launch one Runge-Kutta stage over every work item of the batch.
@@ -175,6 +198,13 @@ cudaError_t launch_get_state(int precision, const DomainDesc* d_desc, long long 
 cudaError_t launch_set_state(int precision, const DomainDesc* d_desc, long long n, const double* H,
                              const double* p, const double* mx, const double* my, const double* C,
                              const double* Fsp, cudaStream_t s);
+
+// Halo rows of the slabs of split domains: for every link (lower slab, upper
+// slab) of `links`, the lower slab's top kHalo interior rows go to the upper
+// slab's lower halo and the upper slab's bottom kHalo rows to the lower
+// slab's upper halo, in state buffer `buffer` (all planes).
+cudaError_t launch_halo(int precision, const void* consts, const int2* links, int nlinks, int max_nx, int buffer,
+                        cudaStream_t s);
 
 // FP64 diagnostics: per-block partial sums (deterministic order) and the final pass.
 constexpr int kDiagThreads = 256;

@@ -7,6 +7,7 @@
 
 #include <cuda.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "device_common.cuh"
@@ -54,11 +55,11 @@ __global__ void init_kernel(const DomainDesc* dd, const double* T, const double*
         s.p = (R)(p ? p[c] : 0.0);
         s.mx = (R)(u ? rho * (1.0 / 3.0) * u[c] : 0.0);
         s.my = (R)(v ? rho * (1.0 / 3.0) * v[c] : 0.0);
-        store_state(reinterpret_cast<R*>(K.st[0]), K.plane, c, s);
+        store_state(reinterpret_cast<R*>(K.st[0]), K.plane, c + K.off, s);
         // previous-step solid fraction from the stored state, in working precision (R14)
         R Tw, Flw;
         invert_enthalpy(K, s.Hh, s.Hl, clamp01(s.Ch + s.Cl), Tw, Flw);
-        reinterpret_cast<R*>(K.Fsp)[c] = R(1) - Flw;
+        reinterpret_cast<R*>(K.Fsp)[c + K.off] = R(1) - Flw;
     }
 }
 
@@ -71,7 +72,7 @@ __global__ void fields_kernel(const DomainDesc* dd, long long n, double* H, doub
     __syncthreads();
     const R* b = reinterpret_cast<const R*>(base);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const SV<R> w = load_state(b, Kd.plane, c);
+        const SV<R> w = load_state(b, Kd.plane, c + Kd.off);
         const double Hd = pair_value(w.Hh, w.Hl), Cd = pair_value(w.Ch, w.Cl);
         double Td, Fld;
         invert_enthalpy(Kd, Hd, 0.0, clamp01(Cd), Td, Fld);
@@ -91,15 +92,15 @@ __global__ void get_state_kernel(const DomainDesc* dd, long long n, double* H, d
                                  double* C, double* Fsp) {
     const R* b = reinterpret_cast<const R*>(dd->st[0]);
     const R* fs = reinterpret_cast<const R*>(dd->Fsp);
-    const long long P = dd->plane;
+    const long long P = dd->plane, off = dd->off;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const SV<R> w = load_state(b, P, c);
+        const SV<R> w = load_state(b, P, c + off);
         if (H) H[c] = pair_value(w.Hh, w.Hl);
         if (p) p[c] = (double)w.p;
         if (mx) mx[c] = (double)w.mx;
         if (my) my[c] = (double)w.my;
         if (C) C[c] = pair_value(w.Ch, w.Cl);
-        if (Fsp) Fsp[c] = (double)fs[c];
+        if (Fsp) Fsp[c] = (double)fs[c + off];
     }
 }
 
@@ -108,9 +109,9 @@ __global__ void set_state_kernel(const DomainDesc* dd, long long n, const double
                                  const double* mx, const double* my, const double* C, const double* Fsp) {
     R* b = reinterpret_cast<R*>(dd->st[0]);
     R* fs = reinterpret_cast<R*>(dd->Fsp);
-    const long long P = dd->plane;
+    const long long P = dd->plane, off = dd->off;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        SV<R> w = load_state(b, P, c);
+        SV<R> w = load_state(b, P, c + off);
         if (sizeof(R) == 8) {
             if (H) w.Hh = (R)H[c];
             if (C) w.Ch = (R)C[c];
@@ -121,9 +122,52 @@ __global__ void set_state_kernel(const DomainDesc* dd, long long n, const double
         if (p) w.p = (R)p[c];
         if (mx) w.mx = (R)mx[c];
         if (my) w.my = (R)my[c];
-        store_state(b, P, c, w);
-        if (Fsp) fs[c] = (R)Fsp[c];
+        store_state(b, P, c + off, w);
+        if (Fsp) fs[c + off] = (R)Fsp[c];
     }
+}
+
+// ---------------------------------------------------------------------------
+// Halo rows of the slabs of split domains.  Link l joins a lower slab A (its
+// top interior rows) and an upper slab B (its bottom interior rows); both
+// have the domain's nx.  Every plane of state buffer `buffer` gets A's rows
+// ny_A - kHalo .. ny_A - 1 in B's halo rows -kHalo .. -1 and B's rows
+// 0 .. kHalo - 1 in A's halo rows ny_A .. ny_A + kHalo - 1.  Plain copies:
+// the halo rows hold the neighbour's values bit for bit.
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void halo_kernel(const Consts<R>* consts, const int2* links, int buffer) {
+    const int2 lk = links[blockIdx.y];
+    const Consts<R>& A = consts[lk.x];
+    const Consts<R>& B = consts[lk.y];
+    const int nx = A.nx;
+    const long long rows = (long long)kHalo * nx, per_dir = (long long)Prec<R>::NP * rows;
+    const R* a_in = reinterpret_cast<const R*>(A.st[buffer]);
+    const R* b_in = reinterpret_cast<const R*>(B.st[buffer]);
+    R* a_out = reinterpret_cast<R*>(A.st[buffer]);
+    R* b_out = reinterpret_cast<R*>(B.st[buffer]);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 2 * per_dir;
+         i += (long long)gridDim.x * blockDim.x) {
+        const bool up = i < per_dir;              // A -> B's lower halo
+        const long long j = up ? i : i - per_dir;
+        const long long k = j / rows, e = j - k * rows;   // plane, element within the kHalo rows
+        if (up)
+            b_out[k * B.plane + B.off - rows + e] = a_in[k * A.plane + A.off + (long long)(A.ny - kHalo) * nx + e];
+        else
+            a_out[k * A.plane + A.off + (long long)A.ny * nx + e] = b_in[k * B.plane + B.off + e];
+    }
+}
+
+cudaError_t launch_halo(int precision, const void* consts, const int2* links, int nlinks, int max_nx, int buffer,
+                        cudaStream_t s) {
+    if (nlinks <= 0) return cudaSuccess;
+    const long long work = 2LL * (precision == 0 ? 5 : 7) * kHalo * max_nx;
+    const dim3 grid((unsigned)std::min<long long>((work + 255) / 256, 1024), (unsigned)nlinks);
+    if (precision == 0)
+        halo_kernel<double><<<grid, 256, 0, s>>>(static_cast<const Consts<double>*>(consts), links, buffer);
+    else
+        halo_kernel<float><<<grid, 256, 0, s>>>(static_cast<const Consts<float>*>(consts), links, buffer);
+    return cudaGetLastError();
 }
 
 static int grid_for(long long n) {
@@ -191,7 +235,7 @@ __global__ void __launch_bounds__(kDiagThreads) diag_partial_kernel(const Domain
     const R* b = reinterpret_cast<const R*>(base);
     double acc[kDiagFields] = {0, 0, 0, 0, 0, 0};
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const SV<R> w = load_state(b, Kd.plane, c);
+        const SV<R> w = load_state(b, Kd.plane, c + Kd.off);
         const double H = pair_value(w.Hh, w.Hl), C = pair_value(w.Ch, w.Cl);
         double T, Fl;
         invert_enthalpy(Kd, H, 0.0, clamp01(C), T, Fl);

@@ -45,6 +45,7 @@ template <> struct Pair<float> { using T = float2; };
 template <> struct Pair<double> { using T = double2; };
 template <class R> using P2 = typename Pair<R>::T;
 
+
 // Derived fields of the ring rows (row r in slot r & 15), paired by the
 // places that read them together: every face point needs (u, v), (rho, C)
 // and (T, C_p); p is needed at every point and mu_c at the cell and outer
@@ -66,10 +67,131 @@ struct Smem {
     // ring of face rows, x-faces of the current chunk
     P2<R> YF[3][RING][32];
     P2<R> XF[3][kChunk][32];
+    // the next rows' stage input, all planes, copied by TMA while the
+    // current chunk computes (planes x rows x columns, as the tensor map's box)
+    // (FP32C only: the FP64 step is bound by the FP64 pipe, not by its loads)
+    alignas(128) R tile[sizeof(R) == 4 ? Prec<R>::NP : 1][kChunk][kTileX];
+    unsigned long long tile_bar;      // mbarrier: the tile's copy has landed
+    int cur_domain;
+    int pre;                          // 1: the tile holds (or is receiving) this item's prologue rows
     Consts<R> K;
 };
 
 __device__ __forceinline__ int slot(int r) { return r & (RING - 1); }
+
+// ---------------------------------------------------------------------------
+// Input tiles by TMA.  One thread issues a 3-D tensor copy (columns x rows x
+// planes) into the shared tile with an mbarrier that counts its bytes; every
+// thread waits on the barrier's phase.  A wait gives up after about 2^31 SM
+// clocks (a second at 2 GHz): the kernel then sets bit 1 of the launch's
+// flag, waits the same bound once more for the copy in flight, and returns.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void bar_init(unsigned long long* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Per-CTA count of the tile copies waited for (the barrier's phase).
+struct TileIO {
+    unsigned phase;
+};
+
+// The first column of a tile: x0 - kHalo rounded down to 16 bytes.
+template <class R>
+__device__ __forceinline__ int tile_x(int x0) { return (x0 - kHalo) & ~(int)(16 / sizeof(R) - 1); }
+
+// Rows [r0, r0 + nrows) of the strip at x0 come from a tile when the domain
+// has tensor maps and every cell of those rows, with the column halo, is
+// inside it (the chunks that need boundary rules load their cells directly).
+template <class R>
+__device__ __forceinline__ bool tile_rows(const Consts<R>& K, int x0, int r0, int nrows) {
+    if constexpr (sizeof(R) != 4) return false;
+    return K.tma && x0 >= kHalo && x0 + kStripX + kHalo <= K.nx && r0 >= -K.hlo && r0 + nrows <= K.ny + K.hhi;
+}
+
+// Thread 0 issues the copy of rows [r0, r0 + kChunk) of domain dom's stage
+// buffer (its tensor map in the launch's map array; hlo: its halo rows below).
+template <class R>
+__device__ __forceinline__ void tile_fetch_from(Smem<R>& S, const StageLaunch& a, int dom, int hlo, int x0, int r0) {
+    const unsigned bar = smem_addr(&S.tile_bar);
+    const unsigned bytes = (unsigned)sizeof(S.tile) + a.tile_probe;
+    const char* map = static_cast<const char*>(a.tmaps) + ((size_t)dom * 3 + a.stage) * kTmapBytes;
+    // the tile's previous contents were read through the generic proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_addr(&S.tile[0][0][0])), "l"(map), "r"(tile_x<R>(x0)), "r"(r0 + hlo), "r"(0), "r"(bar)
+        : "memory");
+}
+
+// The same for the current domain.
+template <class R>
+__device__ __forceinline__ void tile_fetch(Smem<R>& S, const StageLaunch& a, int x0, int r0) {
+    if (threadIdx.x == 0) tile_fetch_from(S, a, S.cur_domain, S.K.hlo, x0, r0);
+}
+
+// During the last chunk of a work item (the tile is free): thread 0 copies
+// the prologue rows of the CTA's next work item, if they come from a tile,
+// and records in S.pre whether it did (read after the next barrier).
+template <class R>
+__device__ __forceinline__ void tile_prefetch_next(Smem<R>& S, const StageLaunch& a, int it) {
+    if (threadIdx.x != 0) return;
+    int pre = 0;
+    const int next = it + gridDim.x;
+    if (next < a.nitems) {
+        const int4 item = a.items[next];
+        const Consts<R>& Kn = static_cast<const Consts<R>*>(a.consts)[item.x];
+        const int x0 = item.y * kStripX, y0 = item.z * a.seg;
+        if (tile_rows(Kn, x0, y0 - kHalo, 2 * kHalo)) {
+            tile_fetch_from(S, a, item.x, Kn.hlo, x0, y0 - kHalo);
+            pre = 1;
+        }
+    }
+    S.pre = pre;
+}
+
+__device__ __forceinline__ bool bar_try_wait(unsigned bar, unsigned parity) {
+    unsigned done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    return done != 0;
+}
+
+// The bounded retry loop (out of line: the tile has normally landed long
+// before its chunk starts, and the first try succeeds).
+__device__ __noinline__ bool bar_wait_bounded(unsigned bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (!bar_try_wait(bar, parity))
+        if (clock64() - t0 > (1LL << 31)) return false;
+    return true;
+}
+
+// Wait for the copy issued last; false if the bound ran out.
+template <class R>
+__device__ __forceinline__ bool tile_wait(Smem<R>& S, TileIO& io) {
+    const unsigned bar = smem_addr(&S.tile_bar), parity = io.phase & 1u;
+    ++io.phase;
+    return bar_try_wait(bar, parity) || bar_wait_bounded(bar, parity);
+}
+
+// The state of tile column cc (0 .. RW-1 of the strip) in row rr.
+__device__ __forceinline__ SV<float> tile_state(const float* t) {
+    constexpr int PS = kChunk * kTileX;
+    SV<float> s;
+    s.Hh = t[0]; s.Hl = t[PS]; s.p = t[2 * PS]; s.mx = t[3 * PS]; s.my = t[4 * PS]; s.Ch = t[5 * PS]; s.Cl = t[6 * PS];
+    return s;
+}
+__device__ __forceinline__ SV<double> tile_state(const double* t) {
+    constexpr int PS = kChunk * kTileX;
+    SV<double> s;
+    s.Hh = t[0]; s.Hl = 0.0; s.p = t[PS]; s.mx = t[2 * PS]; s.my = t[3 * PS]; s.Ch = t[4 * PS]; s.Cl = 0.0;
+    return s;
+}
 
 // Step 1: rows [r0, r0 + nrows) of the strip (all RW columns).
 template <class R>
@@ -86,9 +208,10 @@ template <class R>
 __device__ __forceinline__ void load_rows(Smem<R>& S, const R* in, int x0, int r0, int nrows) {
     const Consts<R>& K = S.K;
     const int total = nrows * RW;
-    if (x0 >= kHalo && x0 + kStripX + kHalo <= K.nx && r0 >= 0 && r0 + nrows <= K.ny) {
-        // every cell of these rows is inside the domain: no boundary mapping
-        const long long base = (long long)r0 * K.nx + (x0 - kHalo);
+    if (x0 >= kHalo && x0 + kStripX + kHalo <= K.nx && r0 >= -K.hlo && r0 + nrows <= K.ny + K.hhi) {
+        // every cell of these rows is inside the domain (or a slab's halo):
+        // no boundary mapping
+        const long long base = (long long)r0 * K.nx + (x0 - kHalo) + K.off;
         for (int idx = threadIdx.x; idx < total; idx += NT) {
             const int rr = idx / RW, cc = idx - rr * RW;
             const SV<R> w = load_state(in, K.plane, base + (long long)rr * K.nx + cc);
@@ -101,8 +224,8 @@ __device__ __forceinline__ void load_rows(Smem<R>& S, const R* in, int x0, int r
         const int gy = r0 + rr, gx = x0 + cc - kHalo;
         int sx, kx, sdx, sy, ky, sdy;
         map_axis(gx, K.nx, K.per_x, XLO, sx, kx, sdx);
-        map_axis(gy, K.ny, K.per_y, YLO, sy, ky, sdy);
-        const SV<R> w = load_state(in, K.plane, (long long)sy * K.nx + sx);
+        map_row(K, gy, sy, ky, sdy);
+        const SV<R> w = load_state(in, K.plane, (long long)sy * K.nx + sx + K.off);
         Prim<R> q = derive(K, w);
         // x sides first, then y (corners); an x ghost takes the wetting of its
         // (interior) row, a y ghost that of its column
@@ -110,6 +233,41 @@ __device__ __forceinline__ void load_rows(Smem<R>& S, const R* in, int x0, int r
         if (ky) apply_ghost(K, sdy, ky, false, wall_wetting(K, in, sdy, gx), q);
         store_prim(S, slot(gy), cc, q);
     }
+}
+
+// Step 1 from a tile: rows [r0, r0 + nrows) (all inside the domain, see
+// tile_rows) read from shared memory instead of global memory.
+template <class R>
+__device__ __forceinline__ void load_rows_tile(Smem<R>& S, int x0, int r0, int nrows) {
+    const Consts<R>& K = S.K;
+    const int xoff = (x0 - kHalo) - tile_x<R>(x0);
+    const int total = nrows * RW;
+    for (int idx = threadIdx.x; idx < total; idx += NT) {
+        const int rr = idx / RW, cc = idx - rr * RW;
+        store_prim(S, slot(r0 + rr), cc, derive(K, tile_state(&S.tile[0][rr][cc + xoff])));
+    }
+}
+
+// The barrier after a load phase; true (on every thread) if some thread's
+// tile wait gave up.  Without tiles (FP64) a plain barrier.
+template <class R>
+__device__ __forceinline__ bool load_barrier_failed(Smem<R>& S, bool ok) {
+    if constexpr (sizeof(R) == 4) {
+        return __syncthreads_or(!ok) != 0;
+    } else {
+        __syncthreads();
+        return false;
+    }
+}
+// A tile wait gave up: report it, wait (with the same bound) for the copy
+// still in flight so that it cannot land in shared memory after the CTA has
+// left, and stop.
+template <class R>
+__device__ __noinline__ bool tile_abort(Smem<R>& S, TileIO& io, int* flag) {
+    if (threadIdx.x == 0) atomicOr(flag, 2);
+    --io.phase;
+    tile_wait(S, io);
+    return false;
 }
 
 // mu_c = 2 beta C (C-1)(2C-1) - kappa lap C (reading R5) at ring offset s0
@@ -140,7 +298,9 @@ __device__ __forceinline__ void muc_rows(Smem<R>& S, int x0, int r0, int nrows) 
     constexpr int NC = RW - 2;
     const int total = nrows * NC;
     const P2<R>* C = &S.P.rc[0][0];
-    if (x0 >= kHalo - 1 && x0 + NC - (kHalo - 1) <= K.nx && r0 >= 0 && r0 + nrows <= K.ny) {
+    // a slab's halo rows take mu_c in place, except the outermost (never read)
+    const int rlo = K.hlo ? 1 - K.hlo : 0, rhi = K.hhi ? K.ny + K.hhi - 1 : K.ny;
+    if (x0 >= kHalo - 1 && x0 + NC - (kHalo - 1) <= K.nx && r0 >= rlo && r0 + nrows <= rhi) {
         // no wall ghost among these cells: the Laplacian in place
         for (int idx = threadIdx.x; idx < total; idx += NT) {
             const int rr = idx / NC, cc = 1 + idx - rr * NC;
@@ -159,7 +319,11 @@ __device__ __forceinline__ void muc_rows(Smem<R>& S, int x0, int r0, int nrows) 
             if (gx < 0) { const int k = -gx; mc = cc + 2 * k - 1; deep |= k > 2; }
             else if (gx >= K.nx) { const int k = gx - K.nx + 1; mc = cc - (2 * k - 1); deep |= k > 2; }
         }
-        if (!K.per_y) {
+        if (gy < 0 && K.hlo) {
+            deep |= gy < rlo;
+        } else if (gy >= K.ny && K.hhi) {
+            deep |= gy >= rhi;
+        } else if (!K.per_y) {
             if (gy < 0) { const int k = -gy; my = gy + 2 * k - 1; deep |= k > 2; }
             else if (gy >= K.ny) { const int k = gy - K.ny + 1; my = gy - (2 * k - 1); deep |= k > 2; }
         }
@@ -286,75 +450,104 @@ __device__ __forceinline__ SideSums<R> side_sums(R un, R ut, R rho, R C, R T, R 
 // w_a over dt_s.  Of the fluxes only the normal momentum flux changes, by
 // cs^2 dt_s (-rho_f cs^2 u_r / r) = -rho_f u_r / (18 r) with the face values;
 // inv_r = 1 / r of the face (0 on the axis, where the face area is zero).
-template <class R, bool AXI>
-__device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const Ring<R>& P, const FaceIdx& x, bool normal_x,
-                                                 bool normal_is_r, R inv_r) {
-    Rec<R> ru, rv, rho, C, T, cp;
-    rec2(&P.uv[0][0], x, ru, rv);
-    const Rec<R>& n = normal_x ? ru : rv;         // normal velocity u_n
-    const Rec<R>& t = normal_x ? rv : ru;         // tangential velocity u_t
-    rec2(&P.rc[0][0], x, rho, C);
-    rec2(&P.tc[0][0], x, T, cp);
+//
+// The arithmetic is written for a value type T (the working precision) and a
+// source Src of the reconstruction pieces (RingFace: one face of the ring).
+template <class T, class R, bool AXI, class Src>
+__device__ __forceinline__ FaceFlux<T> face_math(const Q4<R>& fc, const Src& src, T inv_r) {
+    Rec<T> n, t, rho, C, T_, cp;
+    src.vel(n, t);               // normal and tangential velocity
+    src.rc(rho, C);
+    src.tc(T_, cp);
 
     // side columns: L (points 1, 5, 8) and R (points 3, 6, 7)
-    const SideSums<R> L = side_sums<R, 1>(n.l, t.l, rho.l, C.l, T.l, cp.l, n.dtl, t.dtl, rho.dtl, C.dtl, T.dtl, cp.dtl);
-    const SideSums<R> Rs = side_sums<R, -1>(n.r, t.r, rho.r, C.r, T.r, cp.r, n.dtr, t.dtr, rho.dtr, C.dtr, T.dtr, cp.dtr);
+    const SideSums<T> L = side_sums<T, 1>(n.l, t.l, rho.l, C.l, T_.l, cp.l, n.dtl, t.dtl, rho.dtl, C.dtl, T_.dtl,
+                                          cp.dtl);
+    const SideSums<T> Rs = side_sums<T, -1>(n.r, t.r, rho.r, C.r, T_.r, cp.r, n.dtr, t.dtr, rho.dtr, C.dtr, T_.dtr,
+                                            cp.dtr);
 
     // face column (e_n = 0): point 0 at the face value, points 2 (e_t = +1)
     // and 4 (e_t = -1) shifted by the mean t-step; there
     // q = e_t u_t + u_t^2 - u_n^2 / 2, and at point 0 q = -u^2 / 2
-    const R stn = R(0.125) * (n.dtl + n.dtr), stt = R(0.125) * (t.dtl + t.dtr);
-    const R str = R(0.125) * (rho.dtl + rho.dtr), stc = R(0.125) * (C.dtl + C.dtr);
-    const R un2 = n.o0 - stn, un4 = n.o0 + stn, ut2 = t.o0 - stt, ut4 = t.o0 + stt;
-    const R q2 = fma(ut2, ut2, fma(R(-0.5) * un2, un2, ut2));
-    const R q4 = fma(ut4, ut4, fma(R(-0.5) * un4, un4, -ut4));
-    const R a4 = (rho.o0 + str) * q4;
-    const R f24s = fma(rho.o0 - str, q2, a4);     // rho q at 2 plus at 4
-    const R f24d = fma(rho.o0 - str, q2, -a4);    // rho q at 2 minus at 4
-    const R c24 = fma(C.o0 - stc, ut2, -((C.o0 + stc) * ut4));   // C e.u at 2 plus at 4
-    const R rho_f = rho.o0;
-    const R ruu0 = rho_f * fma(n.o0, n.o0, t.o0 * t.o0);       // -2 rho q at point 0
+    const T stn = T(0.125) * (n.dtl + n.dtr), stt = T(0.125) * (t.dtl + t.dtr);
+    const T str = T(0.125) * (rho.dtl + rho.dtr), stc = T(0.125) * (C.dtl + C.dtr);
+    const T un2 = n.o0 - stn, un4 = n.o0 + stn, ut2 = t.o0 - stt, ut4 = t.o0 + stt;
+    const T q2 = fma(ut2, ut2, fma(T(-0.5) * un2, un2, ut2));
+    const T q4 = fma(ut4, ut4, fma(T(-0.5) * un4, un4, -ut4));
+    const T a4 = (rho.o0 + str) * q4;
+    const T f24s = fma(rho.o0 - str, q2, a4);     // rho q at 2 plus at 4
+    const T f24d = fma(rho.o0 - str, q2, -a4);    // rho q at 2 minus at 4
+    const T c24 = fma(C.o0 - stc, ut2, -((C.o0 + stc) * ut4));   // C e.u at 2 plus at 4
+    const T rho_f = rho.o0;
+    const T ruu0 = rho_f * fma(n.o0, n.o0, t.o0 * t.o0);       // -2 rho q at point 0
 
-    Rec<R> p, muc;
-    rec2(&P.pm[0][0], x, p, muc);
-    R lamf, muf;
-    face_value2(&P.lm[0][0], x, lamf, muf);
-    const Q4<R> fc = ld4(K.facec);   // Q, C_ref / 6, 6 / C_ref, tau_g - 1/2
+    Rec<T> p, muc;
+    src.pm(p, muc);
+    T lamf, muf;
+    src.lm(lamf, muf);
+    const T fQ = T(fc.x), fC = T(fc.y), fI = T(fc.z);   // Q, C_ref / 6, 6 / C_ref; fc.w = tau_g - 1/2
 
     // Eq. 56 and the moments of the surrounding equilibria; weights 4/9, 1/9
     // (e_n or e_t zero) and 1/36 (diagonal)
-    const R w1 = R(1.0 / 9.0), w5 = R(1.0 / 36.0);
-    const R pf = R(2.0 / 3.0) * p.o0 + R(1.0 / 6.0) * (p.l + p.r) - R(2.0 / 9.0) * ruu0 +
+    const T w1 = T(1.0 / 9.0), w5 = T(1.0 / 36.0);
+    const T pf = T(2.0 / 3.0) * p.o0 + T(1.0 / 6.0) * (p.l + p.r) - T(2.0 / 9.0) * ruu0 +
                  w1 * ((L.f0 + Rs.f0) + f24s) + w5 * (L.fs + Rs.fs);
-    const R mn = R(1.0 / 6.0) * (p.l - p.r) + w1 * (L.f0 - Rs.f0) + w5 * (L.fs - Rs.fs);
-    const R mt = R(-1.0 / 24.0) * (p.dtl + p.dtr) + w1 * f24d + w5 * (L.fd + Rs.fd);
-    const R Cf = C.o0 + fc.x * (R(0.5) * (muc.l + muc.r) - muc.o0) + R(1.0 / 3.0) * ((L.c0 - Rs.c0) + c24) +
-                 R(1.0 / 12.0) * (L.cs + Rs.cs);
-    const R Sg = R(0.5) * fc.x * (muc.l - muc.r) + R(1.0 / 3.0) * (L.c0 + Rs.c0) + R(1.0 / 12.0) * (L.cs - Rs.cs);
-    const R Sh = fc.y * (T.l - T.r) + R(1.0 / 3.0) * (L.h0 - Rs.h0) + R(1.0 / 12.0) * (L.hs - Rs.hs);
-    const R Snn_p = R(1.0 / 6.0) * (p.l + p.r);
-    const R Snt_p = R(1.0 / 72.0) * (p.dtr - p.dtl);
-    const R Snn_q = w1 * (L.q0 + Rs.q0) + w5 * (L.qs + Rs.qs);
-    const R Snt_q = w5 * (L.qd - Rs.qd);
+    const T mn = T(1.0 / 6.0) * (p.l - p.r) + w1 * (L.f0 - Rs.f0) + w5 * (L.fs - Rs.fs);
+    const T mt = T(-1.0 / 24.0) * (p.dtl + p.dtr) + w1 * f24d + w5 * (L.fd + Rs.fd);
+    const T Cf = C.o0 + fQ * (T(0.5) * (muc.l + muc.r) - muc.o0) + T(1.0 / 3.0) * ((L.c0 - Rs.c0) + c24) +
+                 T(1.0 / 12.0) * (L.cs + Rs.cs);
+    const T Sg = T(0.5) * fQ * (muc.l - muc.r) + T(1.0 / 3.0) * (L.c0 + Rs.c0) + T(1.0 / 12.0) * (L.cs - Rs.cs);
+    const T Sh = fC * (T_.l - T_.r) + T(1.0 / 3.0) * (L.h0 - Rs.h0) + T(1.0 / 12.0) * (L.hs - Rs.hs);
+    const T Snn_p = T(1.0 / 6.0) * (p.l + p.r);
+    const T Snt_p = T(1.0 / 72.0) * (p.dtr - p.dtl);
+    const T Snn_q = w1 * (L.q0 + Rs.q0) + w5 * (L.qs + Rs.qs);
+    const T Snt_q = w5 * (L.qd - Rs.qd);
     // rho_f cs^2 u_f = sum e f^eq (Eq. 56); tau from the face properties (R9)
-    const R irf = wdiv(R(1), rho_f);
-    const R unf = R(3) * mn * irf, utf = R(3) * mt * irf;
-    const R th = fc.z * lamf * irf;              // tau_h - 0.5 = lambda / (rho C_ref cs^2 dt_s)
-    const R tf = R(6) * muf * irf;               // tau_f - 0.5 = mu / (rho cs^2 dt_s)
-    const R tg = fc.w;
-    const R cs2 = R(1.0 / 3.0);
-    FaceFlux<R> F;
+    const T irf = wdiv(T(1), rho_f);
+    const T unf = T(3) * mn * irf, utf = T(3) * mt * irf;
+    const T th = fI * lamf * irf;                // tau_h - 0.5 = lambda / (rho C_ref cs^2 dt_s)
+    const T tf = T(6) * muf * irf;               // tau_f - 0.5 = mu / (rho cs^2 dt_s)
+    const T tg = T(fc.w);
+    const T cs2 = T(1.0 / 3.0);
+    FaceFlux<T> F;
     // h* = (1.5 - tau) h^eq(x_f) + (tau - 0.5) h^eq(x_f - e dt_s) (Eq. 13, 16)
-    F.Fh = (R(1) - th) * (cp.o0 * T.o0) * unf + th * Sh;
+    F.Fh = (T(1) - th) * (cp.o0 * T_.o0) * unf + th * Sh;
     F.Fp = mn;                                    // sum e_n f^eq(x_f) = rho_f cs^2 u_n,f
     // f* = (1.5 - tau_f) f^eq(x_f) + (tau_f - 0.5) f^eq-m (Eq. 35, 37 with R3)
-    F.Fmn = (R(1) - tf) * cs2 * (pf + rho_f * unf * unf) + tf * (Snn_p + rho_f * Snn_q);
-    F.Fmt = (R(1) - tf) * cs2 * rho_f * unf * utf + tf * (Snt_p + rho_f * Snt_q);
-    F.Fc = (R(1) - tg) * Cf * unf + tg * Sg;     // Eq. 44, 46
+    F.Fmn = (T(1) - tf) * cs2 * (pf + rho_f * unf * unf) + tf * (Snn_p + rho_f * Snn_q);
+    F.Fmt = (T(1) - tf) * cs2 * rho_f * unf * utf + tf * (Snt_p + rho_f * Snt_q);
+    F.Fc = (T(1) - tg) * Cf * unf + tg * Sg;     // Eq. 44, 46
     F.un = unf;
-    if (AXI) F.Fmn += R(-1.0 / 18.0) * rho_f * (normal_is_r ? n.o0 : t.o0) * inv_r;
+    if (AXI) F.Fmn += T(-1.0 / 18.0) * rho_f * src.radial(n.o0, t.o0) * inv_r;
     return F;
 }
+
+// The pieces of one face from the ring, in the working precision.
+template <class R>
+struct RingFace {
+    const Ring<R>& P;
+    const FaceIdx& x;
+    bool normal_x, normal_is_r;
+    __device__ __forceinline__ void vel(Rec<R>& n, Rec<R>& t) const {
+        Rec<R> ru, rv;
+        rec2(&P.uv[0][0], x, ru, rv);
+        n = normal_x ? ru : rv;
+        t = normal_x ? rv : ru;
+    }
+    __device__ __forceinline__ void rc(Rec<R>& a, Rec<R>& b) const { rec2(&P.rc[0][0], x, a, b); }
+    __device__ __forceinline__ void tc(Rec<R>& a, Rec<R>& b) const { rec2(&P.tc[0][0], x, a, b); }
+    __device__ __forceinline__ void pm(Rec<R>& a, Rec<R>& b) const { rec2(&P.pm[0][0], x, a, b); }
+    __device__ __forceinline__ void lm(R& a, R& b) const { face_value2(&P.lm[0][0], x, a, b); }
+    __device__ __forceinline__ R radial(R n0, R t0) const { return normal_is_r ? n0 : t0; }
+};
+
+template <class R, bool AXI>
+__device__ __forceinline__ FaceFlux<R> face_flux(const Consts<R>& K, const Ring<R>& P, const FaceIdx& x, bool normal_x,
+                                                 bool normal_is_r, R inv_r) {
+    const RingFace<R> src{P, x, normal_x, normal_is_r};
+    return face_math<R, R, AXI>(ld4(K.facec), src, inv_r);
+}
+
 
 // ---------------------------------------------------------------------------
 // General streaming steps (reading R26): h, f and g take their surrounding
@@ -614,7 +807,7 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
                                             R irc, int* flag) {
     const Consts<R>& K = S.K;
     const int gx = x0 + lane;
-    const long long c = (long long)r * K.nx + gx;
+    const long long c = (long long)r * K.nx + gx + K.off;
     const int q = slot(r) * RW + lane + kHalo;
     const int qn = slot(r + 1) * RW + lane + kHalo, qs = slot(r - 1) * RW + lane + kHalo;
     const int sr = slot(r), sn = slot(r + 1);
@@ -715,8 +908,10 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
 
 // One work item: the strip segment [x0, x0 + 31) x [y0, y1) of the domain
 // whose constants are in S.K (planar or axisymmetric, fixed per domain).
+// Returns false if a wait for an input tile gave up (the kernel then stops).
 template <class R, bool AXI, bool GEN>
-__device__ __forceinline__ void sweep_item(Smem<R>& S, const StageLaunch& a, int x0, int y0, int y1) {
+__device__ __forceinline__ bool sweep_item(Smem<R>& S, const StageLaunch& a, TileIO& io, int it, int x0, int y0,
+                                           int y1) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const R* in = reinterpret_cast<const R*>(S.K.st[a.stage]);
     // a lane keeps its column through the item: in an axisymmetric domain
@@ -726,16 +921,39 @@ __device__ __forceinline__ void sweep_item(Smem<R>& S, const StageLaunch& a, int
     const R ir_f = (AXI && x0 + lane > 0) ? wdiv(R(1), (R)(x0 + lane)) : R(0);
 
     // prologue: rows y0-3 .. y0+2, mu_c of rows y0-2 .. y0+1, y-face row y0
-    load_rows(S, in, x0, y0 - kHalo, 2 * kHalo);
-    __syncthreads();
+    bool ok = true;
+    if (tile_rows(S.K, x0, y0 - kHalo, 2 * kHalo)) {
+        if (!S.pre) tile_fetch(S, a, x0, y0 - kHalo);   // else copied during the previous item
+        ok = tile_wait(S, io);
+        load_rows_tile(S, x0, y0 - kHalo, 2 * kHalo);
+    } else {
+        load_rows(S, in, x0, y0 - kHalo, 2 * kHalo);
+    }
+    if (load_barrier_failed<R>(S, ok)) return tile_abort(S, io, a.flag);
+    // the first chunk's rows arrive while the prologue computes
+    if (tile_rows(S.K, x0, y0 + kHalo, kChunk)) tile_fetch(S, a, x0, y0 + kHalo);
     muc_rows<R, AXI>(S, x0, y0 - 2, 4);
     __syncthreads();
     if (warp == 0 && lane < kStripX) y_face<R, AXI, GEN>(S, y0, lane, AXI ? ir_c : R(0));
     // (the first chunk writes other ring rows: no barrier needed here)
 
     for (int j0 = y0; j0 < y1; j0 += kChunk) {
-        load_rows(S, in, x0, j0 + kHalo, kChunk);     // rows j0+3 .. j0+10
-        __syncthreads();
+        // rows j0+3 .. j0+10: from the tile copied during the previous chunk,
+        // or directly where boundary rules apply
+        if (tile_rows(S.K, x0, j0 + kHalo, kChunk)) {
+            ok = tile_wait(S, io);
+            load_rows_tile(S, x0, j0 + kHalo, kChunk);
+        } else {
+            load_rows(S, in, x0, j0 + kHalo, kChunk);
+        }
+        if (load_barrier_failed<R>(S, ok)) return tile_abort(S, io, a.flag);
+        // the tile is free again: copy the next chunk's rows behind this one,
+        // or after the last chunk the next work item's prologue rows
+        if (j0 + kChunk < y1) {
+            if (tile_rows(S.K, x0, j0 + kChunk + kHalo, kChunk)) tile_fetch(S, a, x0, j0 + kChunk + kHalo);
+        } else if constexpr (sizeof(R) == 4) {
+            tile_prefetch_next(S, a, it);
+        }
         muc_rows<R, AXI>(S, x0, j0 + 2, kChunk);      // rows j0+2 .. j0+9
         __syncthreads();
         // one face at a time per thread (x then y) keeps register use low
@@ -750,41 +968,48 @@ __device__ __forceinline__ void sweep_item(Smem<R>& S, const StageLaunch& a, int
             cell_update<R, AXI>(S, a.stage, x0, r, warp, lane, ir_c, a.flag);
         __syncthreads();
     }
+    return true;
 }
 
 }  // namespace
 
 template <class R>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) stage_kernel(StageLaunch a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem<R>& S = *reinterpret_cast<Smem<R>*>(smem_raw);
-    __shared__ int cur_domain;
     const int tid = threadIdx.x;
-    if (tid == 0) cur_domain = -1;
+    if (tid == 0) {
+        S.cur_domain = -1;
+        S.pre = 0;
+        bar_init(&S.tile_bar);
+    }
     __syncthreads();
     const Consts<R>* consts = static_cast<const Consts<R>*>(a.consts);
+    TileIO io{0u};
 
     for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
         const int4 item = a.items[it];
-        const int prev = cur_domain;   // read by every thread before the barrier below
-        __syncthreads();               // the previous item is done with shared memory
+        const int prev = S.cur_domain;   // read by every thread before the barrier below
+        __syncthreads();                 // the previous item is done with shared memory
         if (item.x != prev) {
             const unsigned* src = reinterpret_cast<const unsigned*>(consts + item.x);
             unsigned* dst = reinterpret_cast<unsigned*>(&S.K);
             for (int k = tid; k < (int)(sizeof(Consts<R>) / 4); k += NT) dst[k] = src[k];
-            if (tid == 0) cur_domain = item.x;
+            if (tid == 0) S.cur_domain = item.x;
             __syncthreads();
         }
         const int x0 = item.y * kStripX;
         const int y0 = item.z * a.seg;
         const int y1 = min(y0 + a.seg, S.K.ny);
+        bool ok;
         if (S.K.gen) {   // some streaming step differs from 1/2 (reading R26)
-            if (S.K.axi) sweep_item<R, true, true>(S, a, x0, y0, y1);
-            else sweep_item<R, false, true>(S, a, x0, y0, y1);
+            if (S.K.axi) ok = sweep_item<R, true, true>(S, a, io, it, x0, y0, y1);
+            else ok = sweep_item<R, false, true>(S, a, io, it, x0, y0, y1);
         } else {
-            if (S.K.axi) sweep_item<R, true, false>(S, a, x0, y0, y1);
-            else sweep_item<R, false, false>(S, a, x0, y0, y1);
+            if (S.K.axi) ok = sweep_item<R, true, false>(S, a, io, it, x0, y0, y1);
+            else ok = sweep_item<R, false, false>(S, a, io, it, x0, y0, y1);
         }
+        if (!ok) return;   // uniform: every thread saw the same __syncthreads_or
     }
 }
 

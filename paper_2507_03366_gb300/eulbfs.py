@@ -92,6 +92,8 @@ SIGNATURES = [
     ("eulbfs_set_memory_budget", ct.c_int, [ct.c_void_p, ct.c_ulonglong]),
     ("eulbfs_domain_bytes", ct.c_ulonglong, [ct.c_int, ct.c_int, ct.c_int]),
     ("eulbfs_add_domain", ct.c_int, [ct.c_void_p, ct.POINTER(Domain), ct.c_longlong, ct.POINTER(ct.c_int)]),
+    ("eulbfs_add_split_domain", ct.c_int, [ct.c_void_p, ct.POINTER(Domain), ct.c_int, ct.c_longlong,
+                                           ct.POINTER(ct.c_int)]),
     ("eulbfs_remove_domain", ct.c_int, [ct.c_void_p, ct.c_int]),
     ("eulbfs_num_slots", ct.c_int, [ct.c_void_p]),
     ("eulbfs_domain_progress", ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]),
@@ -109,6 +111,7 @@ SIGNATURES = [
     ("eulbfs_use_graphs", ct.c_int, [ct.c_void_p, ct.c_int]),
     ("eulbfs_autotune", ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_float)]),
     ("eulbfs_set_tile", ct.c_int, [ct.c_void_p, ct.c_int]),
+    ("eulbfs_set_tile_wait_probe", ct.c_int, [ct.c_void_p, ct.c_int]),
     ("eulbfs_autotune_report", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int), ct.POINTER(ct.c_float), ct.c_int,
                                           ct.POINTER(ct.c_int)]),
     ("eulbfs_diagnostics_noalloc", ct.c_int, [ct.c_int, ct.c_void_p, ct.c_int, ct.c_int, ct.POINTER(Props),
@@ -226,6 +229,27 @@ class Solver:
         self.shapes[slot.value] = (case.ny, case.nx)
         self.cases[slot.value] = case
         return slot.value
+
+    def add_split(self, case, k: int, max_steps: int = 0) -> List[int]:
+        """Add `case` split along y into k slabs; returns their slots (bottom first)."""
+        keep: list = []
+        d = domain_struct(case, keep)
+        slots = (ct.c_int * k)()
+        _check(lib().eulbfs_add_split_domain(self._h, ct.byref(d), k, max_steps, slots))
+        out = [slots[i] for i in range(k)]
+        for i, sl in enumerate(out):
+            y0, y1 = i * case.ny // k, (i + 1) * case.ny // k
+            while len(self.shapes) <= sl:
+                self.shapes.append(None)
+                self.cases.append(None)
+            self.shapes[sl] = (y1 - y0, case.nx)
+            self.cases[sl] = case
+        return out
+
+    def split_fields(self, slots: Sequence[int]) -> dict:
+        """Fields of a split domain, its slabs stacked back along y."""
+        parts = [self.fields(sl) for sl in slots]
+        return {k: np.concatenate([p[k] for p in parts], axis=0) for k in parts[0]}
 
     def remove(self, slot: int):
         _check(lib().eulbfs_remove_domain(self._h, slot))

@@ -420,3 +420,29 @@ def test_solvers_on_two_host_threads():
     for key in serial:
         for f in FIELDS:
             assert np.array_equal(threaded[key][f], serial[key][f]), (key, f)
+
+
+def test_bounded_tile_wait_reports_timeout_and_context_survives():
+    """Failure detection without a fault: with the wait probe on, every TMA
+    tile barrier expects 16 bytes that never arrive, each wait gives up after
+    its bound (about a second of SM clocks), the kernel stops and the host
+    reads ETIMEOUT.  The context stays usable: a new solver on the same case
+    then matches a third, fresh one bit for bit."""
+    import time
+    case = wl.droplet(96, theta_deg=90.0, St=0.3)     # nx = 96: tensor maps and two interior strips
+    s = eulbfs.Solver([case], precision=eulbfs.FP32C)
+    eulbfs._check(eulbfs.lib().eulbfs_set_tile_wait_probe(s._h, 1))
+    t0 = time.perf_counter()
+    s.step(1)
+    with pytest.raises(eulbfs.EulbfsError) as e:
+        s.sync()
+    assert e.value.code == eulbfs.ETIMEOUT
+    assert time.perf_counter() - t0 < 60.0
+    s.close()
+    a = eulbfs.Solver([case], precision=eulbfs.FP32C)
+    a.step(5)
+    a.sync()
+    b = eulbfs.Solver([case], precision=eulbfs.FP32C)
+    b.step(5)
+    for f in FIELDS:
+        assert np.array_equal(a.fields()[f], b.fields()[f]), f
