@@ -28,7 +28,7 @@ WT = [mpf(4) / 9] + [mpf(1) / 9] * 4 + [mpf(1) / 36] * 4
 GHOST = 2
 
 # boundary kinds (the values of the C ABI)
-PERIODIC, DIRICHLET_T, ADIABATIC, NOSLIP, SYMMETRY, OUTLET, NOFLUX, WETTING = range(8)
+PERIODIC, DIRICHLET_T, ADIABATIC, NOSLIP, SYMMETRY, OUTLET, NOFLUX, WETTING, WETTING_HYST = range(9)
 
 FIELDS = ("H", "T", "Fl", "Cp", "rho", "lam", "mu", "p", "u", "v", "C")
 
@@ -177,17 +177,58 @@ class Grid:
                 return -v
             if sd.flow == SYMMETRY and name == normal:
                 return -v
-        if name == "C" and sd.phase == WETTING:
+        if name == "C" and sd.phase in (WETTING, WETTING_HYST):
             # reading R11: dC/dn_out = (4 cos(theta) / xi) C (1 - C) at distance 2k - 1
-            c = N(math.cos(sd.theta_deg * (math.pi / 180.0)))
+            c = self._cos_theta(side) if sd.phase == WETTING_HYST else N(math.cos(sd.theta_deg * (math.pi / 180.0)))
             return v + (2 * k - 1) * (4 * c / self.m.xi) * v * (1 - v)
         return v
+
+    def _cos_theta(self, side):
+        """Reading R25 (contact-angle hysteresis, Sec. 3.5): the apparent angle
+        of the wall position now being filled, read from the phase field of
+        the two wall layers: cos = (C_0 - C_1) / |grad C|, the tangential
+        derivative a central difference along layer 0 (one-sided where the
+        tangential axis ends at a wall, wrapped where it is periodic), clamped
+        to [cos theta_adv, cos theta_rec]; the equilibrium angle where the
+        wall cell carries no interface (C_0 (1 - C_0) < 1e-3)."""
+        sd = self.m.sides[side]
+        C = self.prim["C"]
+        nx, ny = self.m.nx, self.m.ny
+        xs = side in ("xlo", "xhi")
+        n = ny if xs else nx
+        per = self.m.per_y if xs else self.m.per_x
+        t = self._t
+        if per:
+            tc, tp, tm = t % n, (t + 1) % n, (t - 1) % n
+        else:
+            tc = min(max(t, 0), n - 1)
+            tp, tm = min(tc + 1, n - 1), max(tc - 1, 0)
+        m = nx if xs else ny
+        l0, l1 = (0, 1) if side in ("xlo", "ylo") else (m - 1, m - 2)
+
+        def at(layer, tt):
+            return C[(layer, tt)] if xs else C[(tt, layer)]
+
+        ceq = N(math.cos(sd.theta_deg * (math.pi / 180.0)))
+        c0 = at(l0, tc)
+        if not (c0 * (1 - c0) >= mpf("1e-3")):
+            return ceq
+        dn = c0 - at(l1, tc)
+        dt = (at(l0, tp) - at(l0, tm)) / (2 if per else (tp - tm))
+        g = mp.sqrt(dn * dn + dt * dt)
+        if not g > 0:
+            return ceq
+        c = dn / g
+        lo = N(math.cos(sd.theta_adv_deg * (math.pi / 180.0)))
+        hi = N(math.cos(sd.theta_rec_deg * (math.pi / 180.0)))
+        return lo if c < lo else (hi if c > hi else c)
 
     def _ghosts(self, names):
         nx, ny = self.m.nx, self.m.ny
         for name in names:
             d = self.prim[name]
             for j in range(ny):               # x sides first, on interior rows
+                self._t = j                   # the wall position (R25)
                 for k in range(1, GHOST + 1):
                     if self.m.per_x:
                         d[(-k, j)] = d[(nx - k, j)]
@@ -196,6 +237,7 @@ class Grid:
                         d[(-k, j)] = self._ghost_rule("xlo", name, k, "u", d[(k - 1, j)])
                         d[(nx - 1 + k, j)] = self._ghost_rule("xhi", name, k, "u", d[(nx - k, j)])
             for i in range(-GHOST, nx + GHOST):   # then y sides on every column
+                self._t = i
                 for k in range(1, GHOST + 1):
                     if self.m.per_y:
                         d[(i, -k)] = d[(i, ny - k)]

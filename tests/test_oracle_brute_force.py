@@ -3,8 +3,9 @@
 Every other face-flux pin uses fields that are uniform, linear or vary in one
 quantity at a time.  Here rho, mu, lambda, C_p (through random H and C in
 the solid, mushy and liquid ranges), T, p, u, v, C and mu_c all vary at
-random on 4x4 and 5x3 grids, with walls of every kind, periodic sides, the
-axisymmetric (r, z) form and per-distribution streaming steps.  The
+random on 4x4, 5x3 and 5x4 grids, with walls of every kind (contact-angle
+hysteresis included), periodic sides, the axisymmetric (r, z) form and
+per-distribution streaming steps.  The
 reference is ``brute_eulbfs``, a second transcription of Sec. 2.5 steps
 (2)-(4) (Eq. 54, 9/29/33/42, 56, 13/16, 35/37, 44/46, 53) and of Eq. 51-52,
 58 written from the paper in 40-digit arithmetic.  The oracle must agree with
@@ -55,6 +56,15 @@ def _axis_walls():
                  wl.Side(wl.ADIABATIC, wl.OUTLET, wl.NOFLUX))
 
 
+def _hysteresis_walls():
+    """Hysteresis windows on three walls (R25): the apparent angles of random
+    fields fall inside and outside them."""
+    return wl.BC(wl.Side(wl.DIRICHLET_T, wl.NOSLIP, wl.WETTING_HYST, -0.3, 70.0, 110.0, 40.0),
+                 wl.Side(wl.ADIABATIC, wl.NOSLIP, wl.WETTING_HYST, 0.0, 95.0, 120.0, 80.0),
+                 wl.Side(wl.DIRICHLET_T, wl.NOSLIP, wl.WETTING_HYST, 0.1, 60.0, 150.0, 30.0),
+                 wl.Side(wl.ADIABATIC, wl.OUTLET, wl.NOFLUX))
+
+
 PER = wl.BC(wl.PER, wl.PER, wl.PER, wl.PER)
 AXI_PER_Y = wl.BC(wl.Side(wl.ADIABATIC, wl.SYMMETRY, wl.NOFLUX), wl.Side(wl.ADIABATIC, wl.NOSLIP, wl.WETTING, 0, 70.0),
                   wl.PER, wl.PER)
@@ -66,6 +76,7 @@ CASES = [
     ("axisymmetric_4x4", 4, 4, AXI_PER_Y, 1, (0.5, 0.5, 0.5), 0.0, 3),
     ("walls_steps_4x4", 4, 4, _walls(), 0, (0.3, 0.4, 0.25), -1e-3, 4),
     ("axisymmetric_steps_5x3", 5, 3, _axis_walls(), 1, (0.35, 0.3, 0.45), -1e-3, 5),
+    ("hysteresis_walls_5x4", 5, 4, _hysteresis_walls(), 0, (0.5, 0.5, 0.5), -1e-3, 8),
 ]
 # Eq. 5-7 as printed (literal_eq7) instead of reading R1
 LITERAL = [("literal_walls_5x3", 5, 3, _walls(), 0, (0.5, 0.5, 0.5), -1e-3, 6),
