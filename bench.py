@@ -248,7 +248,8 @@ def workload_config(cases, world: int, args) -> dict:
                         f"{{128,192,256,384,512}}, {cells} cells per GPU",
             "global_batch": len(cases) * world, "seq_len": cells, "parallelism": f"independent domains x{world}",
             "precision": "FP32C",
-            "work_item": (f"31x{args.tile} strip segment" + (" (autotuned)" if getattr(args, "autotuned", False) else ""))
+            "work_item": (f"31-column strips, rows cut into runs of about {args.tile}"
+                          + (" (autotuned)" if getattr(args, "autotuned", False) else ""))
             if args.tile else "31-column strip segments, height autotuned", "graph_steps": args.graph,
             "l2": (f"working set {cells * 28 * 3 / 1e6:.0f} MB > L2 (129 MB): three 28 B/cell state buffers, "
                    "no flush needed" if cells * 28 * 3 > 129e6 else

@@ -294,8 +294,11 @@ int eulbfs_launches_per_step(const eulbfs_solver* s);
 int eulbfs_use_graphs(eulbfs_solver* s, int steps_per_graph);
 
 /* Work-item shape of the stage kernel: each item is a 31-column strip of a
- * domain, `rows` cells high (a multiple of 8 in [8, 1024]; 0 = 64).  Results
- * do not depend on it. */
+ * domain and a run of its rows.  `rows` (a multiple of 8 in [8, 1024];
+ * 0 = 64) is the target height: a domain of ny rows is cut into
+ * round(ny / rows) runs (at least one) of nearly equal height, in whole
+ * 8-row chunks.  The persistent CTAs claim items from a counter, tallest
+ * first.  Results do not depend on it. */
 int eulbfs_set_tile(eulbfs_solver* s, int rows);
 
 /* Diagnostics of a caller-held domain state that allocates no device memory.
@@ -331,11 +334,11 @@ int eulbfs_diagnostics_noalloc(int precision, const void* state, int nx, int ny,
                                const eulbfs_props* props, double* out, void* stream);
 
 /* Pick the work-item height of the current batch by timing each candidate
- * (16, 32, 64, 128, 256 rows) over steps_per_candidate steps on the solver's
- * stream, in two rounds, and keeping the candidate with the fastest of its
- * two timings (*best_ms_per_step).  The timed steps are real steps of every
- * active domain (results do not depend on the height), so the simulation
- * advances by 2 * 5 * (steps_per_candidate + 1) steps.  Synchronises the
+ * (24, 32, 40, 48, 64, 96, 128, 256 rows) over steps_per_candidate steps on
+ * the solver's stream, in two rounds, and keeping the candidate with the
+ * fastest of its two timings (*best_ms_per_step).  The timed steps are real
+ * steps of every active domain (results do not depend on the height), so the
+ * simulation advances by 2 * 8 * (steps_per_candidate + 1) steps.  Synchronises the
  * stream.  EULBFS_EINVAL for a null solver or steps_per_candidate < 1; a
  * failing step returns its error and leaves the height unchanged. */
 int eulbfs_autotune(eulbfs_solver* s, int steps_per_candidate, int* best_rows, float* best_ms_per_step);

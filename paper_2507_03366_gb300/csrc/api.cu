@@ -167,6 +167,8 @@ size_t domain_bytes(long long n, int precision) {
 
 int eulbfs::set_error(int code, const char* msg) { return fail(code, msg); }
 
+constexpr int kMaxTune = 8;   // autotune candidates kept for eulbfs_autotune_report
+
 struct eulbfs_solver {
     int precision = EULBFS_FP32C;
     cudaStream_t stream = nullptr;
@@ -198,8 +200,8 @@ struct eulbfs_solver {
     bool graph_valid = false;
     // the last eulbfs_autotune: candidate heights and their best ms per step
     int tune_n = 0;
-    int tune_rows[8] = {};
-    float tune_ms[8] = {};
+    int tune_rows[kMaxTune] = {};
+    float tune_ms[kMaxTune] = {};
     unsigned tile_probe = 0;       // eulbfs_set_tile_wait_probe
     // split domains: (lower slab, upper slab) pairs whose halo rows are
     // exchanged after every stage; the active ones on the device
@@ -304,15 +306,24 @@ int rebuild(eulbfs_solver* s) {
         s->consts_cap = std::max(img.size(), 2 * s->consts_cap);
         CK(cudaMalloc(&s->d_consts, s->consts_cap), "constants array");
     }
+    // work items: each domain's kChunk-row chunks split into round(ny / seg)
+    // runs of nearly equal length; the list runs the tallest items first, so
+    // that the persistent CTAs, which claim items in list order, end on the
+    // shortest
     std::vector<int4> items;
     for (int k = 0; k < nd; ++k) {
         Dom& d = s->doms[k];
+        const int chunks = (d.grid.ny + kChunk - 1) / kChunk, per = std::max(1, s->seg / kChunk);
         d.desc.strips = (d.grid.nx + kStripX - 1) / kStripX;
-        d.desc.segs = (d.grid.ny + s->seg - 1) / s->seg;
+        d.desc.segs = std::min(chunks, std::max(1, (chunks + per / 2) / per));
         if (!d.active()) continue;
-        for (int sy = 0; sy < d.desc.segs; ++sy)
-            for (int sx = 0; sx < d.desc.strips; ++sx) items.push_back(make_int4(k, sx, sy, 0));
+        for (int sy = 0; sy < d.desc.segs; ++sy) {
+            const int y0 = (int)((long long)sy * chunks / d.desc.segs) * kChunk;
+            const int y1 = std::min(d.grid.ny, (int)((long long)(sy + 1) * chunks / d.desc.segs) * kChunk);
+            for (int sx = 0; sx < d.desc.strips; ++sx) items.push_back(make_int4(k, sx, y0, y1));
+        }
     }
+    std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.w - a.z > b.w - b.z; });
     if (!img.empty()) CK(cudaMemcpyAsync(s->d_consts, img.data(), img.size(), cudaMemcpyHostToDevice, s->stream), "upload constants");
     s->nitems = (int)items.size();
     if (s->nitems > s->items_cap) {
@@ -353,8 +364,9 @@ int launch_step_direct(eulbfs_solver* s) {
     a.tile_probe = s->tile_probe;
     a.items = s->d_items;
     a.nitems = s->nitems;
-    a.seg = s->seg;
     a.flag = s->d_flag;
+    a.work = s->d_flag + 1;
+    if (cudaMemsetAsync(a.work, 0, 3 * sizeof(int), s->stream) != cudaSuccess) return cuda_fail(cudaGetLastError(), "work counters");
     static const char* const kStageRange[3] = {"eulbfs RK stage 1", "eulbfs RK stage 2", "eulbfs RK stage 3"};
     for (int st = 0; st < 3; ++st) {
         a.stage = st;
@@ -510,13 +522,13 @@ int new_solver(int precision, void* stream, eulbfs_solver** out) {
         }
         s->own_stream = true;
     }
-    if (cudaMalloc(&s->d_flag, sizeof(int)) != cudaSuccess || cudaMallocHost(&s->h_flag, sizeof(int)) != cudaSuccess ||
+    if (cudaMalloc(&s->d_flag, 4 * sizeof(int)) != cudaSuccess || cudaMallocHost(&s->h_flag, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&s->d_diag, sizeof(double) * kDiagFields) != cudaSuccess ||
         cudaMallocHost(&s->h_diag, sizeof(double) * kDiagFields) != cudaSuccess) {
         eulbfs_destroy(s);
         return fail(EULBFS_ENOMEM, "solver allocation failed");
     }
-    cudaMemsetAsync(s->d_flag, 0, sizeof(int), s->stream);
+    cudaMemsetAsync(s->d_flag, 0, 4 * sizeof(int), s->stream);
     *out = s;
     return EULBFS_OK;
 }
@@ -618,7 +630,8 @@ int eulbfs_set_tile(eulbfs_solver* s, int rows) {
 int eulbfs_autotune(eulbfs_solver* s, int steps_per_candidate, int* best_rows, float* best_ms_per_step) {
     if (!s) return fail(EULBFS_EINVAL, "null solver");
     if (steps_per_candidate < 1) return fail(EULBFS_EINVAL, "steps_per_candidate must be >= 1");
-    static const int kCandidates[] = {16, 32, 64, 128, 256};
+    static const int kCandidates[] = {24, 32, 40, 48, 64, 96, 128, 256};
+    static_assert(sizeof(kCandidates) / sizeof(kCandidates[0]) <= kMaxTune, "report arrays");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0), "event");
     CK(cudaEventCreate(&e1), "event");
@@ -650,7 +663,7 @@ int eulbfs_autotune(eulbfs_solver* s, int steps_per_candidate, int* best_rows, f
     s->tune_n = 0;
     for (int k = 0; k < kNC; ++k) {
         if (cand_ms[k] > 0.f && (best_ms == 0.f || cand_ms[k] < best_ms)) { best_ms = cand_ms[k]; best = kCandidates[k]; }
-        if (cand_ms[k] > 0.f && s->tune_n < 8) {
+        if (cand_ms[k] > 0.f && s->tune_n < kMaxTune) {
             s->tune_rows[s->tune_n] = kCandidates[k];
             s->tune_ms[s->tune_n] = cand_ms[k];
             ++s->tune_n;

@@ -154,7 +154,7 @@ __host__ __device__ inline void fill_consts(const DomainDesc& d, Consts<R>& K) {
 }
 
 // Stage kernel geometry: a work item is a strip segment of one domain,
-// kStripX interior columns wide and `seg` rows high, swept in chunks of
+// kStripX interior columns wide and rows [y0, y1) high, swept in chunks of
 // kChunk rows (one warp per row, so kChunk warps per CTA).
 constexpr int kStripX = 31;   // 31 cells -> 32 x-faces per row: one per lane
 constexpr int kChunk = 8;
@@ -170,10 +170,10 @@ constexpr int kTmapBytes = 128;   // sizeof(CUtensorMap)
 struct StageLaunch {
     const void* consts;      // Consts<R>[ndomains] in device memory
     const void* tmaps;       // CUtensorMap[ndomains][3]: one per state buffer (used where Consts::tma)
-    const int4* items;       // (domain, strip, segment, 0)
+    const int4* items;       // (domain, strip, y0, y1), tallest first
     int nitems;
     int stage;               // 0, 1, 2
-    int seg;                 // segment height in rows (multiple of kChunk)
+    int* work;               // per-stage item counters, zeroed before each step
     int* flag;               // bit 0: non-finite state seen; bit 1: a bounded wait for a tile gave up
     unsigned tile_probe;     // bytes each tile barrier expects beyond its copy (0; > 0 only to test the bounded waits)
 };

@@ -73,6 +73,7 @@ struct Smem {
     alignas(128) R tile[sizeof(R) == 4 ? Prec<R>::NP : 1][kChunk][kTileX];
     unsigned long long tile_bar;      // mbarrier: the tile's copy has landed
     int cur_domain;
+    int next;                         // the CTA's next work item
     int pre;                          // 1: the tile holds (or is receiving) this item's prologue rows
     Consts<R> K;
 };
@@ -142,17 +143,52 @@ template <class R>
 __device__ __forceinline__ void tile_prefetch_next(Smem<R>& S, const StageLaunch& a, int it) {
     if (threadIdx.x != 0) return;
     int pre = 0;
-    const int next = it + gridDim.x;
+    const int next = S.next;
     if (next < a.nitems) {
         const int4 item = a.items[next];
         const Consts<R>& Kn = static_cast<const Consts<R>*>(a.consts)[item.x];
-        const int x0 = item.y * kStripX, y0 = item.z * a.seg;
+        const int x0 = item.y * kStripX, y0 = item.z;
         if (tile_rows(Kn, x0, y0 - kHalo, 2 * kHalo)) {
             tile_fetch_from(S, a, item.x, Kn.hlo, x0, y0 - kHalo);
             pre = 1;
         }
     }
     S.pre = pre;
+}
+
+// The cell update reads W^n and dF_s/dt (stages 2 and 3) or F_s^{n-1}
+// (stage 1) straight from global memory, where nothing has touched them
+// during the step.  One warp asks L2 for rows r0 .. r0+7 of those arrays
+// a chunk before their update: lane l takes row r0 + l % 8 and arrays
+// l / 8 and l / 8 + 4 (the 7 state planes, then dF_s/dt), both ends of the
+// strip's segment of each row.  Prefetches are hints: they change no value.
+__device__ __forceinline__ void l2_prefetch(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
+}
+
+template <class R>
+__device__ __forceinline__ void prefetch_update_rows(const Consts<R>& K, int stage, int x0, int r0, int y1, int lane) {
+    const int r = r0 + (lane & 7);
+    if (r >= y1) return;
+    const long long c0 = (long long)r * K.nx + K.off + x0;
+    const long long c1 = (long long)r * K.nx + K.off + min(x0 + kStripX, K.nx) - 1;
+    const int k = lane >> 3;
+    if (stage == 0) {
+        if (k == 0) {
+            const R* f = reinterpret_cast<const R*>(K.Fsp);
+            l2_prefetch(f + c0);
+            l2_prefetch(f + c1);
+        }
+        return;
+    }
+    const R* w = reinterpret_cast<const R*>(K.st[0]);
+    l2_prefetch(w + k * K.plane + c0);
+    l2_prefetch(w + k * K.plane + c1);
+    const R* b = k + 4 < Prec<R>::NP ? w + (k + 4) * K.plane : reinterpret_cast<const R*>(K.dFs);
+    if (k + 4 <= Prec<R>::NP) {
+        l2_prefetch(b + c0);
+        l2_prefetch(b + c1);
+    }
 }
 
 __device__ __forceinline__ bool bar_try_wait(unsigned bar, unsigned parity) {
@@ -932,6 +968,8 @@ __device__ __forceinline__ bool sweep_item(Smem<R>& S, const StageLaunch& a, Til
     if (load_barrier_failed<R>(S, ok)) return tile_abort(S, io, a.flag);
     // the first chunk's rows arrive while the prologue computes
     if (tile_rows(S.K, x0, y0 + kHalo, kChunk)) tile_fetch(S, a, x0, y0 + kHalo);
+    if constexpr (sizeof(R) == 4)
+        if (warp == NT / 32 - 1) prefetch_update_rows(S.K, a.stage, x0, y0, y1, lane);
     muc_rows<R, AXI>(S, x0, y0 - 2, 4);
     __syncthreads();
     if (warp == 0 && lane < kStripX) y_face<R, AXI, GEN>(S, y0, lane, AXI ? ir_c : R(0));
@@ -954,6 +992,10 @@ __device__ __forceinline__ bool sweep_item(Smem<R>& S, const StageLaunch& a, Til
         } else if constexpr (sizeof(R) == 4) {
             tile_prefetch_next(S, a, it);
         }
+        // the next chunk's update rows into L2 (FP32C: the FP64 step is
+        // bound by its FP64 arithmetic)
+        if constexpr (sizeof(R) == 4)
+            if (warp == NT / 32 - 1 && j0 + kChunk < y1) prefetch_update_rows(S.K, a.stage, x0, j0 + kChunk, y1, lane);
         muc_rows<R, AXI>(S, x0, j0 + 2, kChunk);      // rows j0+2 .. j0+9
         __syncthreads();
         // one face at a time per thread (x then y) keeps register use low
@@ -987,10 +1029,13 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) stage_kernel(Stage
     const Consts<R>* consts = static_cast<const Consts<R>*>(a.consts);
     TileIO io{0u};
 
-    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+    // the first wave takes items 0 .. grid-1; after that each CTA claims its
+    // next item from the stage's counter when it starts an item
+    for (int it = blockIdx.x; it < a.nitems;) {
         const int4 item = a.items[it];
         const int prev = S.cur_domain;   // read by every thread before the barrier below
         __syncthreads();                 // the previous item is done with shared memory
+        if (tid == 0) S.next = gridDim.x + atomicAdd(a.work + a.stage, 1);
         if (item.x != prev) {
             const unsigned* src = reinterpret_cast<const unsigned*>(consts + item.x);
             unsigned* dst = reinterpret_cast<unsigned*>(&S.K);
@@ -999,8 +1044,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) stage_kernel(Stage
             __syncthreads();
         }
         const int x0 = item.y * kStripX;
-        const int y0 = item.z * a.seg;
-        const int y1 = min(y0 + a.seg, S.K.ny);
+        const int y0 = item.z, y1 = item.w;
         bool ok;
         if (S.K.gen) {   // some streaming step differs from 1/2 (reading R26)
             if (S.K.axi) ok = sweep_item<R, true, true>(S, a, io, it, x0, y0, y1);
@@ -1010,6 +1054,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) stage_kernel(Stage
             else ok = sweep_item<R, false, false>(S, a, io, it, x0, y0, y1);
         }
         if (!ok) return;   // uniform: every thread saw the same __syncthreads_or
+        it = S.next;       // written before the item's barriers
     }
 }
 
