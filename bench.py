@@ -49,11 +49,11 @@ BYTES_STAGE_BY_STAGE = {1: 244, 0: 352}
 # captured again.
 KERNEL_SOURCES = ("stage.cu", "device_common.cuh", "eulbfs_internal.h")
 COUNTERS = {
-    "sources_sha256": "f639c69a82e7e078b7f90223fbe16528e60a87d8b146e20246aeb1bb5d74bda9",
-    "fp32_flops_per_cell_stage": {"rz": 946.0, "xy": 908.1},
-    "warp_inst_per_cell_stage": {"rz": 44.72, "xy": 43.37},
-    "dram_bytes_per_cell_launch": {"rz": 64.9, "xy": 64.8},
-    "fp64_flops_per_cell_stage": {"rz": 1023.6, "xy": 949.3},
+    "sources_sha256": "9951096500acc887bf85669c9f0cef19049ff316a44d25c0a2ea48dc0246cfbe",
+    "fp32_flops_per_cell_stage": {"rz": 953.3, "xy": 914.8},
+    "warp_inst_per_cell_stage": {"rz": 45.83, "xy": 44.43},
+    "dram_bytes_per_cell_launch": {"rz": 66.7, "xy": 66.8},
+    "fp64_flops_per_cell_stage": {"rz": 1035.7, "xy": 958.0},
 }
 # Streaming steps (dt_h, dt_f, dt_g) of the general-face-path leg.
 GEN_STEPS = (0.3, 0.4, 0.3)

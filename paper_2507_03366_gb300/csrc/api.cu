@@ -168,6 +168,7 @@ size_t domain_bytes(long long n, int precision) {
 int eulbfs::set_error(int code, const char* msg) { return fail(code, msg); }
 
 constexpr int kMaxTune = 8;   // autotune candidates kept for eulbfs_autotune_report
+constexpr int kTailLevels = 2;   // halvings of the work list's last wave
 
 struct eulbfs_solver {
     int precision = EULBFS_FP32C;
@@ -323,7 +324,27 @@ int rebuild(eulbfs_solver* s) {
             for (int sx = 0; sx < d.desc.strips; ++sx) items.push_back(make_int4(k, sx, y0, y1));
         }
     }
-    std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.w - a.z > b.w - b.z; });
+    const auto taller = [](const int4& a, const int4& b) { return a.w - a.z > b.w - b.z; };
+    std::stable_sort(items.begin(), items.end(), taller);
+    // the end of the list in shorter items: kTailLevels times, the last wave
+    // (one item per resident CTA) is cut in half, so the launch ends on items
+    // 2^-kTailLevels as tall and the first CTAs to run out of work wait less
+    // for the last
+    const int resident = stage_blocks_per_sm(s->precision) * s->sms;
+    for (int level = 0; level < kTailLevels && (long long)items.size() > 2LL * resident; ++level) {
+        std::vector<int4> tail;
+        for (size_t i = items.size() - resident; i < items.size(); ++i) {
+            const int4 t = items[i];
+            const int chunks = (t.w - t.z + kChunk - 1) / kChunk;
+            if (chunks < 2) { tail.push_back(t); continue; }
+            const int ym = t.z + (chunks / 2) * kChunk;
+            tail.push_back(make_int4(t.x, t.y, t.z, ym));
+            tail.push_back(make_int4(t.x, t.y, ym, t.w));
+        }
+        items.resize(items.size() - resident);
+        std::stable_sort(tail.begin(), tail.end(), taller);
+        items.insert(items.end(), tail.begin(), tail.end());
+    }
     if (!img.empty()) CK(cudaMemcpyAsync(s->d_consts, img.data(), img.size(), cudaMemcpyHostToDevice, s->stream), "upload constants");
     s->nitems = (int)items.size();
     if (s->nitems > s->items_cap) {
