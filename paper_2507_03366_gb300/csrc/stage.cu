@@ -311,8 +311,7 @@ __device__ __noinline__ bool tile_abort(Smem<R>& S, TileIO& io, int* flag) {
 // is the 5-point one, or in an axisymmetric domain the conservative
 // (1/r) d/dr (r dC/dr) + d2C/dz2 with faces at r = gx and gx + 1.
 template <class R, bool AXI>
-__device__ __forceinline__ R chem_potential(const Consts<R>& K, const P2<R>* RC, int s0, int sN, int sS, int gx) {
-    const R c = RC[s0].y, ce = RC[s0 + 1].y, cw = RC[s0 - 1].y, cn = RC[sN].y, cs = RC[sS].y;
+__device__ __forceinline__ R chem_potential_of(const Consts<R>& K, R c, R ce, R cw, R cn, R cs, int gx) {
     R lap;
     if (AXI) {
         const R rw = (R)gx, re = rw + R(1);
@@ -322,6 +321,52 @@ __device__ __forceinline__ R chem_potential(const Consts<R>& K, const P2<R>* RC,
     }
     const Q4<R> cc = ld4(K.cellc2);   // 2 beta, kappa
     return cc.x * c * (c - R(1)) * (R(2) * c - R(1)) - cc.y * lap;
+}
+
+template <class R, bool AXI>
+__device__ __forceinline__ R chem_potential(const Consts<R>& K, const P2<R>* RC, int s0, int sN, int sS, int gx) {
+    return chem_potential_of<R, AXI>(K, RC[s0].y, RC[s0 + 1].y, RC[s0 - 1].y, RC[sN].y, RC[sS].y, gx);
+}
+
+// True if mu_c of rows [r0, r0 + nrows) of the strip involves no wall ghost
+// (the in-place Laplacian of muc_rows' first branch applies to all of them).
+template <class R>
+__device__ __forceinline__ bool muc_in_place(const Consts<R>& K, int x0, int r0, int nrows) {
+    const int rlo = K.hlo ? 1 - K.hlo : 0, rhi = K.hhi ? K.ny + K.hhi - 1 : K.ny;
+    return x0 >= kHalo - 1 && x0 + (RW - 2) - (kHalo - 1) <= K.nx && r0 >= rlo && r0 + nrows <= rhi;
+}
+
+// Steps 1 and 2 of an interior chunk from its tile (FP32C): rows
+// [r0, r0 + kChunk) derived as in load_rows_tile and, by the same threads,
+// mu_c of rows [r0 - 1, r0 + kChunk - 1) (muc_in_place must hold).  Their
+// C comes from the tile (rows >= r0, C_hi + C_lo as derive forms it) or
+// from the ring (rows r0 - 2, r0 - 1, derived by the previous chunk), so
+// mu_c needs no barrier after the derive; the values are those muc_rows
+// computes.
+template <class R, bool AXI>
+__device__ __forceinline__ void load_rows_tile_muc(Smem<R>& S, int x0, int r0, bool with_muc) {
+    const Consts<R>& K = S.K;
+    constexpr int PS = kChunk * kTileX;
+    const int xoff = (x0 - kHalo) - tile_x<R>(x0);
+    const R* t = &S.tile[0][0][0];
+    for (int idx = threadIdx.x; idx < kChunk * RW; idx += NT) {
+        const int rr = idx / RW, cc = idx - rr * RW;
+        store_prim(S, slot(r0 + rr), cc, derive(K, tile_state(t + rr * kTileX + cc + xoff)));
+    }
+    if (!with_muc) return;
+    // mu_c of ring row r0 + m, m = -1 .. kChunk-2, columns 1 .. RW-2
+    const P2<R>* RC = &S.P.rc[0][0];
+    constexpr int NC = RW - 2;
+    for (int idx = threadIdx.x; idx < kChunk * NC; idx += NT) {
+        const int m = idx / NC - 1, cc = 1 + idx - (m + 1) * NC;
+        // C of row r0 + k at column cc + d: the tile for k >= 0, the ring below
+        auto Cat = [&](int k, int d) -> R {
+            const int ti = k * kTileX + cc + d + xoff;
+            return k >= 0 ? t[5 * PS + ti] + t[6 * PS + ti] : RC[slot(r0 + k) * RW + cc + d].y;
+        };
+        S.P.pm[slot(r0 + m)][cc].y =
+            chem_potential_of<R, AXI>(K, Cat(m, 0), Cat(m, 1), Cat(m, -1), Cat(m + 1, 0), Cat(m - 1, 0), x0 + cc - kHalo);
+    }
 }
 
 // Step 2: mu_c for rows [r0, r0 + nrows), columns 1 .. RW-2.  A wall ghost
@@ -978,9 +1023,11 @@ __device__ __forceinline__ bool sweep_item(Smem<R>& S, const StageLaunch& a, Til
     for (int j0 = y0; j0 < y1; j0 += kChunk) {
         // rows j0+3 .. j0+10: from the tile copied during the previous chunk,
         // or directly where boundary rules apply
+        bool muc_done = false;
         if (tile_rows(S.K, x0, j0 + kHalo, kChunk)) {
             ok = tile_wait(S, io);
-            load_rows_tile(S, x0, j0 + kHalo, kChunk);
+            if constexpr (sizeof(R) == 4) muc_done = muc_in_place(S.K, x0, j0 + 2, kChunk);
+            load_rows_tile_muc<R, AXI>(S, x0, j0 + kHalo, muc_done);
         } else {
             load_rows(S, in, x0, j0 + kHalo, kChunk);
         }
@@ -996,8 +1043,10 @@ __device__ __forceinline__ bool sweep_item(Smem<R>& S, const StageLaunch& a, Til
         // bound by its FP64 arithmetic)
         if constexpr (sizeof(R) == 4)
             if (warp == NT / 32 - 1 && j0 + kChunk < y1) prefetch_update_rows(S.K, a.stage, x0, j0 + kChunk, y1, lane);
-        muc_rows<R, AXI>(S, x0, j0 + 2, kChunk);      // rows j0+2 .. j0+9
-        __syncthreads();
+        if (!muc_done) {   // rows j0+2 .. j0+9
+            muc_rows<R, AXI>(S, x0, j0 + 2, kChunk);
+            __syncthreads();
+        }
         // one face at a time per thread (x then y) keeps register use low
 #pragma unroll 1
         for (int k = 0; k < 2; ++k) {
