@@ -53,7 +53,7 @@ COUNTERS = {
     "sources_sha256": "9951096500acc887bf85669c9f0cef19049ff316a44d25c0a2ea48dc0246cfbe",
     "fp32_flops_per_cell_stage": {"rz": 947.8, "xy": 909.7},
     "warp_inst_per_cell_stage": {"rz": 45.23, "xy": 43.87},
-    "dram_bytes_per_cell_launch": {"rz": 81.6, "xy": 81.4},
+    "dram_bytes_per_cell_step": {"rz": 244.9, "xy": 244.2},
     "fp64_flops_per_cell_stage": {"rz": 1025.1, "xy": 949.8},
 }
 # Streaming steps (dt_h, dt_f, dt_g) of the general-face-path leg.
@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--tile", type=int, default=0,
                     help="rows per work item (strip segment height); 0: picked by eulbfs_autotune on the batch")
     ap.add_argument("--graph", type=int, default=10, help="steps per captured CUDA graph (0: direct launches)")
+    ap.add_argument("--stage-launches", action="store_true",
+                    help="one launch per Runge-Kutta stage instead of one per time step")
     ap.add_argument("--fp64-steps", type=int, default=30)
     ap.add_argument("--gen-steps", type=int, default=200,
                     help="steps of the general-streaming-step leg (0: skip)")
@@ -252,6 +254,7 @@ def workload_config(cases, world: int, args) -> dict:
             "work_item": (f"31-column strips, rows cut into runs of about {args.tile}"
                           + (" (autotuned)" if getattr(args, "autotuned", False) else ""))
             if args.tile else "31-column strip segments, height autotuned", "graph_steps": args.graph,
+            "launch": "one per Runge-Kutta stage" if args.stage_launches else "one per time step",
             "l2": (f"working set {cells * 28 * 3 / 1e6:.0f} MB > L2 (129 MB): three 28 B/cell state buffers, "
                    "no flush needed" if cells * 28 * 3 > 129e6 else
                    f"working set {cells * 28 * 3 / 1e6:.0f} MB, not larger than L2 (129 MB)")}
@@ -276,19 +279,20 @@ def measure_fma_peaks(stream) -> dict:
     return out
 
 
-def roofline(cells, geometry, per_launch_ms, hbm_gbs, peaks) -> dict:
-    """The stage kernel's roofs; the top level names the one with the largest
+def roofline(cells, geometry, ms_per_step, launches_per_step, hbm_gbs, peaks) -> dict:
+    """The stage kernel's roofs over a time step (one launch per step, or
+    one per Runge-Kutta stage); the top level names the one with the largest
     fraction, which is the one the kernel meets first."""
     current = counters_current()
-    s = per_launch_ms * 1e-3
+    s = ms_per_step * 1e-3
     hbm = {}
     for key, b, what in (("compulsory", BYTES_COMPULSORY[1], "state read and written once per step"),
-                         ("stage_by_stage", BYTES_STAGE_BY_STAGE[1], "a kernel per Runge-Kutta stage")):
-        ach = b / STAGES * cells / s / 1e9
+                         ("stage_by_stage", BYTES_STAGE_BY_STAGE[1], "each Runge-Kutta stage's input and output")):
+        ach = b * cells / s / 1e9
         hbm[key] = {"bytes_per_cell_step": b, "meaning": what, "achieved": ach, "peak": hbm_gbs, "unit": "GB/s",
                     "frac": ach / hbm_gbs}
-    dram = COUNTERS["dram_bytes_per_cell_launch"][geometry] * cells if current else None
-    hbm["dram_measured"] = {"bytes_per_cell_launch": COUNTERS["dram_bytes_per_cell_launch"][geometry] if current else None,
+    dram = COUNTERS["dram_bytes_per_cell_step"][geometry] * cells if current else None
+    hbm["dram_measured"] = {"bytes_per_cell_step": COUNTERS["dram_bytes_per_cell_step"][geometry] if current else None,
                             "achieved": dram / s / 1e9 if dram else None, "peak": hbm_gbs, "unit": "GB/s",
                             "frac": dram / s / 1e9 / hbm_gbs if dram else None}
     roofs = {"hbm_" + k: dict(v, bound="hbm", peak_source="measured copy bandwidth (MEASURED_PEAKS.json)")
@@ -296,8 +300,8 @@ def roofline(cells, geometry, per_launch_ms, hbm_gbs, peaks) -> dict:
     if peaks:
         fp32_peak = max(peaks["fp32"]["tflops"], peaks["fp32x2"]["tflops"])
         issue_peak = peaks["fp32"]["fma_warp_inst_per_s"]
-        flops = COUNTERS["fp32_flops_per_cell_stage"][geometry] * cells if current else None
-        inst = COUNTERS["warp_inst_per_cell_stage"][geometry] * cells if current else None
+        flops = COUNTERS["fp32_flops_per_cell_stage"][geometry] * STAGES * cells if current else None
+        inst = COUNTERS["warp_inst_per_cell_stage"][geometry] * STAGES * cells if current else None
         roofs["fp32"] = {"bound": "alu", "flops_per_cell_stage": COUNTERS["fp32_flops_per_cell_stage"][geometry]
                          if current else None, "achieved": flops / s / 1e12 if flops else None, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": flops / s / 1e12 / fp32_peak if flops else None,
@@ -309,9 +313,10 @@ def roofline(cells, geometry, per_launch_ms, hbm_gbs, peaks) -> dict:
                                          "FMA-chain kernel (one FFMA per lane per instruction)"}
     top = max((v for v in roofs.values() if v.get("frac") is not None), key=lambda v: v["frac"])
     return {"bound": top["bound"], "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
-            "frac": top["frac"], "traffic": dram, "binding_roof": next(k for k, v in roofs.items() if v is top),
-            "kernel": "eulbfs::stage_kernel<float>", "avg_launch_ms": per_launch_ms,
-            "counters_current": current, "roofs": roofs}
+            "frac": top["frac"], "traffic": dram / launches_per_step if dram else None,
+            "binding_roof": next(k for k, v in roofs.items() if v is top),
+            "kernel": "eulbfs::stage_kernel<float>", "launches_per_step": launches_per_step,
+            "avg_launch_ms": ms_per_step / launches_per_step, "counters_current": current, "roofs": roofs}
 
 
 def run_reference(args):
@@ -385,6 +390,7 @@ def main():
         args.autotuned = True
         tuning = {str(k): v for k, v in sorted(sol.autotune_report().items())}
     sol.set_tile(args.tile)
+    sol.set_whole_step(not args.stage_launches)
     if args.graph:
         sol.use_graphs(args.graph)
     for _ in range(max(3, args.warmup)):
@@ -411,11 +417,11 @@ def main():
     ms_max = reduce_max(ms, world)
     total_cells = reduce_sum(float(cells), world)
     value = total_cells * args.steps / (ms_max * 1e-3) / 1e9
-    launches = STAGES * args.steps
+    launches = sol.launches_per_step() * args.steps
 
     mp = measured_peaks()
     hbm = mp["hbm_gbs"] if mp else 6800.0
-    roof = roofline(cells, args.geometry, ms / launches, hbm, peaks)
+    roof = roofline(cells, args.geometry, ms / args.steps, sol.launches_per_step(), hbm, peaks)
     if not mp:
         for v in roof["roofs"].values():
             if v.get("unit") == "GB/s":

@@ -285,9 +285,21 @@ int eulbfs_load(eulbfs_solver* s, int slot, const void* buf, unsigned long long 
 int eulbfs_diagnostics(eulbfs_solver* s, int slot, eulbfs_diag* d);
 
 /* Number of kernels the solver launches per time step of the current batch:
- * three stage launches, and a halo copy after each while a split domain's
- * slabs are active. */
+ * one whole-step launch (eulbfs_set_whole_step); three stage launches with
+ * it off; and while a split domain's slabs are active, three stage launches
+ * with a halo copy after each. */
 int eulbfs_launches_per_step(const eulbfs_solver* s);
+
+/* One launch per time step (on = 1, the default) or one per Runge-Kutta
+ * stage (on = 0).  A whole-step launch runs the work items of stage 1, then
+ * stage 2, then stage 3 (Eq. 58), each item as soon as the items of the
+ * previous stage whose output it reads (its strip and the strips beside it,
+ * its rows and 4 rows beyond) are done, so one stage's last items overlap
+ * the next stage's first.  Batches with split domains always launch per
+ * stage (their halo copies run between stages).  Results are the same bit
+ * for bit.  A wait for a neighbour's item is bounded (about a second) and
+ * reports EULBFS_ETIMEOUT like a tile wait.  Errors: EINVAL. */
+int eulbfs_set_whole_step(eulbfs_solver* s, int on);
 
 /* Capture eulbfs_step's per-step launches in a CUDA graph of `steps_per_graph`
  * steps (0 disables); replays are used when n is a multiple of it. */

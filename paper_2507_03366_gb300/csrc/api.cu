@@ -187,6 +187,15 @@ struct eulbfs_solver {
     int sms = 1;
     int grid = 1;
     int* d_flag = nullptr;
+    // item counters ([0..3]) and the whole-step launch's done flags ([3][nitems])
+    int* d_sched = nullptr;
+    int sched_cap = 0;
+    // whole-step launches: each item's neighbourhood (CSR: offsets, then indices)
+    int* d_deps = nullptr;
+    int deps_cap = 0;
+    int ndeps = 0;
+    bool whole_step = true;        // eulbfs_set_whole_step: one launch per step where possible
+    bool fused = false;            // this batch runs whole-step launches
     int* h_flag = nullptr;
     int* h_flags = nullptr;        // pinned, one per slot: per-domain non-finite flags
     int h_flags_cap = 0;
@@ -278,6 +287,57 @@ std::vector<unsigned char> consts_image(const std::vector<Dom>& doms, const std:
 
 // Rebuild the work list (strip segments of every active domain) and the
 // per-domain constants after the set of domains or the segment height changed.
+// A whole-step launch runs the items of stage s once the stage s - 1 items
+// they read are done.  Item i reads its strip and the strips on either side
+// (the 3-column halo, and the wall-wetting column beyond), rows
+// [y0 - 4, y1 + 4) (the 3-row halo and the wall-wetting row beyond), both
+// wrapped on periodic axes: those are the items listed here (CSR).
+void build_deps(const eulbfs_solver* s, const std::vector<int4>& items, std::vector<int>& dep) {
+    const int n = (int)items.size();
+    std::vector<std::vector<std::vector<int>>> by(s->doms.size());   // [domain][strip] -> items
+    for (int i = 0; i < n; ++i) {
+        const int4& t = items[i];
+        auto& v = by[t.x];
+        if (v.empty()) v.resize(s->doms[t.x].desc.strips);
+        v[t.y].push_back(i);
+    }
+    dep.assign(n + 1, 0);
+    std::vector<char> mark;
+    for (int i = 0; i < n; ++i) {
+        const int4& t = items[i];
+        const DomainDesc& d = s->doms[t.x].desc;
+        mark.assign(d.strips, 0);
+        const int x0 = t.y * kStripX;
+        for (int c = x0 - kHalo - 1; c < x0 + kStripX + kHalo + 1; ++c) {
+            int cc = c;
+            if (d.per_x) cc = ((c % d.nx) + d.nx) % d.nx;
+            else if (c < 0 || c >= d.nx) continue;
+            mark[cc / kStripX] = 1;
+        }
+        // row intervals of [y0 - 4, y1 + 4) within [0, ny)
+        int iv[2][2];
+        int niv = 0;
+        const int lo = t.z - kHalo - 1, hi = t.w + kHalo + 1;
+        if (!d.per_y || hi - lo >= d.ny) {
+            iv[0][0] = std::max(0, lo); iv[0][1] = std::min(d.ny, hi); niv = 1;
+        } else {
+            const int a = ((lo % d.ny) + d.ny) % d.ny, b = a + (hi - lo);
+            if (b <= d.ny) { iv[0][0] = a; iv[0][1] = b; niv = 1; }
+            else { iv[0][0] = a; iv[0][1] = d.ny; iv[1][0] = 0; iv[1][1] = b - d.ny; niv = 2; }
+        }
+        for (int sx = 0; sx < d.strips; ++sx) {
+            if (!mark[sx]) continue;
+            for (int j : by[t.x][sx]) {
+                const int4& u = items[j];
+                bool hit = false;
+                for (int k = 0; k < niv; ++k) hit |= u.z < iv[k][1] && iv[k][0] < u.w;
+                if (hit) dep.push_back(j);
+            }
+        }
+        dep[i + 1] = (int)dep.size() - (n + 1);
+    }
+}
+
 int rebuild(eulbfs_solver* s) {
     const int nd = (int)s->doms.size();
     // tensor maps of every live domain's three state buffers
@@ -369,6 +429,28 @@ int rebuild(eulbfs_solver* s) {
         CK(cudaMalloc(&s->d_links, sizeof(int2) * s->links_cap), "halo links");
     }
     if (s->nlinks) CK(cudaMemcpyAsync(s->d_links, act.data(), sizeof(int2) * s->nlinks, cudaMemcpyHostToDevice, s->stream), "upload links");
+    // counters and done flags; the neighbourhoods of a whole-step launch
+    // (split domains exchange halos between stages: one launch per stage)
+    const int sched = 4 + 3 * s->nitems;
+    if (sched > s->sched_cap) {
+        if (s->d_sched) cudaFree(s->d_sched);
+        s->d_sched = nullptr;
+        s->sched_cap = std::max(sched, 2 * s->sched_cap);
+        CK(cudaMalloc(&s->d_sched, sizeof(int) * s->sched_cap), "work counters");
+    }
+    s->fused = s->whole_step && s->nlinks == 0 && s->nitems > 0;
+    std::vector<int> dep;
+    if (s->fused) {
+        build_deps(s, items, dep);
+        s->ndeps = (int)dep.size();
+        if (s->ndeps > s->deps_cap) {
+            if (s->d_deps) cudaFree(s->d_deps);
+            s->d_deps = nullptr;
+            s->deps_cap = std::max(s->ndeps, 2 * s->deps_cap);
+            CK(cudaMalloc(&s->d_deps, sizeof(int) * s->deps_cap), "item neighbourhoods");
+        }
+        CK(cudaMemcpyAsync(s->d_deps, dep.data(), sizeof(int) * s->ndeps, cudaMemcpyHostToDevice, s->stream), "upload neighbourhoods");
+    }
     // the host vectors die here: make the copies complete before returning
     CK(cudaStreamSynchronize(s->stream), "rebuild sync");
     const int per_sm = stage_blocks_per_sm(s->precision);
@@ -386,8 +468,22 @@ int launch_step_direct(eulbfs_solver* s) {
     a.items = s->d_items;
     a.nitems = s->nitems;
     a.flag = s->d_flag;
-    a.work = s->d_flag + 1;
-    if (cudaMemsetAsync(a.work, 0, 3 * sizeof(int), s->stream) != cudaSuccess) return cuda_fail(cudaGetLastError(), "work counters");
+    a.work = s->d_sched;
+    a.done = s->d_sched + 4;
+    a.dep_off = s->d_deps;
+    a.dep_idx = s->d_deps + (s->nitems + 1);
+    a.stage = 0;
+    // counters (and done flags) start at zero every step: an aborted step cannot leave one behind
+    const size_t zero = sizeof(int) * (s->fused ? 4 + 3 * (size_t)s->nitems : 4);
+    if (cudaMemsetAsync(s->d_sched, 0, zero, s->stream) != cudaSuccess) return cuda_fail(cudaGetLastError(), "work counters");
+    if (s->fused) {
+        a.stages = 3;
+        nvtxRangePushA("eulbfs step");
+        const cudaError_t e = launch_stage(s->precision, a, s->grid, s->stream);
+        nvtxRangePop();
+        return e == cudaSuccess ? EULBFS_OK : cuda_fail(e, "stage kernel launch");
+    }
+    a.stages = 1;
     static const char* const kStageRange[3] = {"eulbfs RK stage 1", "eulbfs RK stage 2", "eulbfs RK stage 3"};
     for (int st = 0; st < 3; ++st) {
         a.stage = st;
@@ -543,13 +639,13 @@ int new_solver(int precision, void* stream, eulbfs_solver** out) {
         }
         s->own_stream = true;
     }
-    if (cudaMalloc(&s->d_flag, 4 * sizeof(int)) != cudaSuccess || cudaMallocHost(&s->h_flag, sizeof(int)) != cudaSuccess ||
+    if (cudaMalloc(&s->d_flag, sizeof(int)) != cudaSuccess || cudaMallocHost(&s->h_flag, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&s->d_diag, sizeof(double) * kDiagFields) != cudaSuccess ||
         cudaMallocHost(&s->h_diag, sizeof(double) * kDiagFields) != cudaSuccess) {
         eulbfs_destroy(s);
         return fail(EULBFS_ENOMEM, "solver allocation failed");
     }
-    cudaMemsetAsync(s->d_flag, 0, 4 * sizeof(int), s->stream);
+    cudaMemsetAsync(s->d_flag, 0, sizeof(int), s->stream);
     *out = s;
     return EULBFS_OK;
 }
@@ -734,7 +830,18 @@ int eulbfs_launches_per_step(const eulbfs_solver* s) {
     const int nd = (int)s->doms.size();
     for (const int2& l : s->links)   // a halo copy after each stage while two linked slabs are active
         if (l.x < nd && l.y < nd && s->doms[l.x].active() && s->doms[l.y].active()) return 6;
-    return 3;
+    bool any = false;
+    for (const Dom& d : s->doms) any |= d.active();
+    return s->whole_step && any ? 1 : 3;
+}
+
+int eulbfs_set_whole_step(eulbfs_solver* s, int on) {
+    if (!s || (on != 0 && on != 1)) return fail(EULBFS_EINVAL, "null solver or on not 0/1");
+    if (s->whole_step != (on == 1)) {
+        s->whole_step = on == 1;
+        s->dirty = true;
+    }
+    return EULBFS_OK;
 }
 
 int eulbfs_add_split_domain(eulbfs_solver* s, const eulbfs_domain* d, int k, long long max_steps, int* slots) {
@@ -1006,6 +1113,8 @@ void eulbfs_destroy(eulbfs_solver* s) {
     if (s->d_consts) cudaFree(s->d_consts);
     if (s->d_tmaps) cudaFree(s->d_tmaps);
     if (s->d_links) cudaFree(s->d_links);
+    if (s->d_sched) cudaFree(s->d_sched);
+    if (s->d_deps) cudaFree(s->d_deps);
     if (s->d_items) cudaFree(s->d_items);
     if (s->d_flag) cudaFree(s->d_flag);
     if (s->h_flag) cudaFreeHost(s->h_flag);

@@ -74,6 +74,8 @@ struct Smem {
     unsigned long long tile_bar;      // mbarrier: the tile's copy has landed
     int cur_domain;
     int next;                         // the CTA's next work item
+    int ready;                        // whole-step launches: the current item's inputs are done
+    int stage, item;                  // the current item's stage and work-list index
     int pre;                          // 1: the tile holds (or is receiving) this item's prologue rows
     Consts<R> K;
 };
@@ -117,10 +119,11 @@ __device__ __forceinline__ bool tile_rows(const Consts<R>& K, int x0, int r0, in
 // Thread 0 issues the copy of rows [r0, r0 + kChunk) of domain dom's stage
 // buffer (its tensor map in the launch's map array; hlo: its halo rows below).
 template <class R>
-__device__ __forceinline__ void tile_fetch_from(Smem<R>& S, const StageLaunch& a, int dom, int hlo, int x0, int r0) {
+__device__ __forceinline__ void tile_fetch_from(Smem<R>& S, const StageLaunch& a, int stage, int dom, int hlo, int x0,
+                                                int r0) {
     const unsigned bar = smem_addr(&S.tile_bar);
     const unsigned bytes = (unsigned)sizeof(S.tile) + a.tile_probe;
-    const char* map = static_cast<const char*>(a.tmaps) + ((size_t)dom * 3 + a.stage) * kTmapBytes;
+    const char* map = static_cast<const char*>(a.tmaps) + ((size_t)dom * 3 + stage) * kTmapBytes;
     // the tile's previous contents were read through the generic proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -132,28 +135,71 @@ __device__ __forceinline__ void tile_fetch_from(Smem<R>& S, const StageLaunch& a
 
 // The same for the current domain.
 template <class R>
-__device__ __forceinline__ void tile_fetch(Smem<R>& S, const StageLaunch& a, int x0, int r0) {
-    if (threadIdx.x == 0) tile_fetch_from(S, a, S.cur_domain, S.K.hlo, x0, r0);
+__device__ __forceinline__ void tile_fetch(Smem<R>& S, const StageLaunch& a, int stage, int x0, int r0) {
+    if (threadIdx.x == 0) tile_fetch_from(S, a, stage, S.cur_domain, S.K.hlo, x0, r0);
+}
+
+// Position g of a launch's item sequence: its stage and work item.
+__device__ __forceinline__ int2 stage_item(const StageLaunch& a, int g) {
+    if (a.stages == 1) return make_int2(a.stage, g);
+    const int st = g / a.nitems;
+    return make_int2(st, g - st * a.nitems);
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Whole-step launches: true once every stage st - 1 item whose output item i
+// of stage st reads is done (acquire loads; the caller's barrier then
+// publishes the data to its CTA).  Lanes of one warp take one neighbour each.
+// A bounded wait: after 2^31 clocks it gives up and returns false.
+__device__ __forceinline__ bool deps_ready(const StageLaunch& a, int st, int i, int lane, bool wait) {
+    // one-stage launches have no neighbourhood lists (kernel boundaries order the stages)
+    if (a.stages == 1 || st == 0) return true;
+    const int* done = a.done + (size_t)(st - 1) * a.nitems;
+    bool ok = true;
+    for (int j = a.dep_off[i] + lane; j < a.dep_off[i + 1]; j += 32) {
+        const int* f = done + a.dep_idx[j];
+        if (ld_acquire(f)) continue;
+        if (!wait) { ok = false; continue; }
+        const long long t0 = clock64();
+        while (!ld_acquire(f)) {
+            if (clock64() - t0 > (1LL << 31)) { ok = false; break; }
+            __nanosleep(256);
+        }
+    }
+    return __all_sync(0xffffffffu, ok);
 }
 
 // During the last chunk of a work item (the tile is free): thread 0 copies
-// the prologue rows of the CTA's next work item, if they come from a tile,
+// the prologue rows of the CTA's next work item, if they come from a tile
+// (and, in a whole-step launch, if the items it reads are already done),
 // and records in S.pre whether it did (read after the next barrier).
 template <class R>
-__device__ __forceinline__ void tile_prefetch_next(Smem<R>& S, const StageLaunch& a, int it) {
-    if (threadIdx.x != 0) return;
+__device__ __forceinline__ void tile_prefetch_next(Smem<R>& S, const StageLaunch& a) {
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
     int pre = 0;
     const int next = S.next;
-    if (next < a.nitems) {
-        const int4 item = a.items[next];
+    if (next < a.nitems * a.stages) {
+        const int2 si = stage_item(a, next);
+        const int4 item = a.items[si.y];
         const Consts<R>& Kn = static_cast<const Consts<R>*>(a.consts)[item.x];
         const int x0 = item.y * kStripX, y0 = item.z;
-        if (tile_rows(Kn, x0, y0 - kHalo, 2 * kHalo)) {
-            tile_fetch_from(S, a, item.x, Kn.hlo, x0, y0 - kHalo);
+        if (tile_rows(Kn, x0, y0 - kHalo, 2 * kHalo) && deps_ready(a, si.x, si.y, lane, false)) {
+            __syncwarp();   // the lanes' acquire loads before lane 0's proxy fence
+            if (lane == 0) {
+                // the rows were written by other CTAs through the generic proxy
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                tile_fetch_from(S, a, si.x, item.x, Kn.hlo, x0, y0 - kHalo);
+            }
             pre = 1;
         }
     }
-    S.pre = pre;
+    if (lane == 0) S.pre = pre;
 }
 
 // The cell update reads W^n and dF_s/dt (stages 2 and 3) or F_s^{n-1}
@@ -298,8 +344,18 @@ __device__ __forceinline__ bool load_barrier_failed(Smem<R>& S, bool ok) {
 // A tile wait gave up: report it, wait (with the same bound) for the copy
 // still in flight so that it cannot land in shared memory after the CTA has
 // left, and stop.
+// A wait for the items an item reads gave up (whole-step launches): report
+// it as a bounded wait that gave up, wait for a prologue tile that may be in
+// flight, and stop.
 template <class R>
-__device__ __noinline__ bool tile_abort(Smem<R>& S, TileIO& io, int* flag) {
+__device__ __noinline__ void dep_abort(Smem<R>& S, TileIO io, int* flag) {
+    if (threadIdx.x == 0) atomicOr(flag, 2);
+    if constexpr (sizeof(R) == 4)
+        if (S.pre) tile_wait(S, io);
+}
+
+template <class R>
+__device__ __noinline__ bool tile_abort(Smem<R>& S, TileIO io, int* flag) {
     if (threadIdx.x == 0) atomicOr(flag, 2);
     --io.phase;
     tile_wait(S, io);
@@ -987,14 +1043,15 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
     store_state(reinterpret_cast<R*>(K.st[stage == 2 ? 0 : stage + 1]), K.plane, c, o);
 }
 
-// One work item: the strip segment [x0, x0 + 31) x [y0, y1) of the domain
-// whose constants are in S.K (planar or axisymmetric, fixed per domain).
-// Returns false if a wait for an input tile gave up (the kernel then stops).
+// One work item of Runge-Kutta stage `stage`: the strip segment
+// [x0, x0 + 31) x [y0, y1) of the domain whose constants are in S.K (planar
+// or axisymmetric, fixed per domain).  Returns false if a wait for an input
+// tile gave up (the kernel then stops).
 template <class R, bool AXI, bool GEN>
-__device__ __forceinline__ bool sweep_item(Smem<R>& S, const StageLaunch& a, TileIO& io, int it, int x0, int y0,
-                                           int y1) {
+__device__ __forceinline__ bool sweep_item(Smem<R>& S, const StageLaunch& a, const int stage, TileIO& io, int x0,
+                                           int y0, int y1) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const R* in = reinterpret_cast<const R*>(S.K.st[a.stage]);
+    const R* in = reinterpret_cast<const R*>(S.K.st[stage]);
     // a lane keeps its column through the item: in an axisymmetric domain
     // 1 / r of its cell centre (y-faces, cell volume) and of its x-face
     // (0 on the axis, where the face area is zero)
@@ -1004,7 +1061,7 @@ __device__ __forceinline__ bool sweep_item(Smem<R>& S, const StageLaunch& a, Til
     // prologue: rows y0-3 .. y0+2, mu_c of rows y0-2 .. y0+1, y-face row y0
     bool ok = true;
     if (tile_rows(S.K, x0, y0 - kHalo, 2 * kHalo)) {
-        if (!S.pre) tile_fetch(S, a, x0, y0 - kHalo);   // else copied during the previous item
+        if (!S.pre) tile_fetch(S, a, stage, x0, y0 - kHalo);   // else copied during the previous item
         ok = tile_wait(S, io);
         load_rows_tile(S, x0, y0 - kHalo, 2 * kHalo);
     } else {
@@ -1012,9 +1069,9 @@ __device__ __forceinline__ bool sweep_item(Smem<R>& S, const StageLaunch& a, Til
     }
     if (load_barrier_failed<R>(S, ok)) return tile_abort(S, io, a.flag);
     // the first chunk's rows arrive while the prologue computes
-    if (tile_rows(S.K, x0, y0 + kHalo, kChunk)) tile_fetch(S, a, x0, y0 + kHalo);
+    if (tile_rows(S.K, x0, y0 + kHalo, kChunk)) tile_fetch(S, a, stage, x0, y0 + kHalo);
     if constexpr (sizeof(R) == 4)
-        if (warp == NT / 32 - 1) prefetch_update_rows(S.K, a.stage, x0, y0, y1, lane);
+        if (warp == NT / 32 - 1) prefetch_update_rows(S.K, stage, x0, y0, y1, lane);
     muc_rows<R, AXI>(S, x0, y0 - 2, 4);
     __syncthreads();
     if (warp == 0 && lane < kStripX) y_face<R, AXI, GEN>(S, y0, lane, AXI ? ir_c : R(0));
@@ -1035,14 +1092,14 @@ __device__ __forceinline__ bool sweep_item(Smem<R>& S, const StageLaunch& a, Til
         // the tile is free again: copy the next chunk's rows behind this one,
         // or after the last chunk the next work item's prologue rows
         if (j0 + kChunk < y1) {
-            if (tile_rows(S.K, x0, j0 + kChunk + kHalo, kChunk)) tile_fetch(S, a, x0, j0 + kChunk + kHalo);
+            if (tile_rows(S.K, x0, j0 + kChunk + kHalo, kChunk)) tile_fetch(S, a, stage, x0, j0 + kChunk + kHalo);
         } else if constexpr (sizeof(R) == 4) {
-            tile_prefetch_next(S, a, it);
+            tile_prefetch_next(S, a);
         }
         // the next chunk's update rows into L2 (FP32C: the FP64 step is
         // bound by its FP64 arithmetic)
         if constexpr (sizeof(R) == 4)
-            if (warp == NT / 32 - 1 && j0 + kChunk < y1) prefetch_update_rows(S.K, a.stage, x0, j0 + kChunk, y1, lane);
+            if (warp == NT / 32 - 1 && j0 + kChunk < y1) prefetch_update_rows(S.K, stage, x0, j0 + kChunk, y1, lane);
         if (!muc_done) {   // rows j0+2 .. j0+9
             muc_rows<R, AXI>(S, x0, j0 + 2, kChunk);
             __syncthreads();
@@ -1056,7 +1113,7 @@ __device__ __forceinline__ bool sweep_item(Smem<R>& S, const StageLaunch& a, Til
         __syncthreads();
         const int r = j0 + warp;
         if (r < y1 && lane < kStripX && x0 + lane < S.K.nx)
-            cell_update<R, AXI>(S, a.stage, x0, r, warp, lane, ir_c, a.flag);
+            cell_update<R, AXI>(S, stage, x0, r, warp, lane, ir_c, a.flag);
         __syncthreads();
     }
     return true;
@@ -1078,32 +1135,62 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) stage_kernel(Stage
     const Consts<R>* consts = static_cast<const Consts<R>*>(a.consts);
     TileIO io{0u};
 
-    // the first wave takes items 0 .. grid-1; after that each CTA claims its
-    // next item from the stage's counter when it starts an item
-    for (int it = blockIdx.x; it < a.nitems;) {
-        const int4 item = a.items[it];
+    // Every item is claimed from the launch's counter, one item ahead (the
+    // tile prefetch of the next item's prologue needs to know it).  In a
+    // whole-step launch the items of stage 1 follow all of stage 0 and those
+    // of stage 2 all of stage 1, and an item waits for the items of the
+    // previous stage it reads.  Only running CTAs hold items, and every item
+    // waits only for items claimed before it, so the earliest unfinished
+    // item can always proceed.
+    int* const counter = a.work + (a.stages == 1 ? a.stage : 0);
+    if (tid == 0) S.next = atomicAdd(counter, 1);
+    __syncthreads();
+    while (S.next < a.nitems * a.stages) {
+        const int2 si = stage_item(a, S.next);
+        const int4 item = a.items[si.y];
         const int prev = S.cur_domain;   // read by every thread before the barrier below
         __syncthreads();                 // the previous item is done with shared memory
-        if (tid == 0) S.next = gridDim.x + atomicAdd(a.work + a.stage, 1);
+        if (tid == 0) {
+            S.next = atomicAdd(counter, 1);
+            S.stage = si.x;
+            S.item = si.y;
+        }
+        if (a.stages > 1 && si.x > 0) {
+            if (tid < 32) {
+                const bool ready = deps_ready(a, si.x, si.y, tid, true);
+                if (tid == 0) S.ready = ready;
+            }
+            __syncthreads();
+            if (!S.ready) return dep_abort(S, io, a.flag);
+            // the rows this item copies by TMA were written through the generic proxy
+            if (tid == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+        }
         if (item.x != prev) {
             const unsigned* src = reinterpret_cast<const unsigned*>(consts + item.x);
             unsigned* dst = reinterpret_cast<unsigned*>(&S.K);
             for (int k = tid; k < (int)(sizeof(Consts<R>) / 4); k += NT) dst[k] = src[k];
             if (tid == 0) S.cur_domain = item.x;
-            __syncthreads();
         }
+        __syncthreads();                 // S.K
         const int x0 = item.y * kStripX;
         const int y0 = item.z, y1 = item.w;
         bool ok;
         if (S.K.gen) {   // some streaming step differs from 1/2 (reading R26)
-            if (S.K.axi) ok = sweep_item<R, true, true>(S, a, io, it, x0, y0, y1);
-            else ok = sweep_item<R, false, true>(S, a, io, it, x0, y0, y1);
+            if (S.K.axi) ok = sweep_item<R, true, true>(S, a, si.x, io, x0, y0, y1);
+            else ok = sweep_item<R, false, true>(S, a, si.x, io, x0, y0, y1);
         } else {
-            if (S.K.axi) ok = sweep_item<R, true, false>(S, a, io, it, x0, y0, y1);
-            else ok = sweep_item<R, false, false>(S, a, io, it, x0, y0, y1);
+            if (S.K.axi) ok = sweep_item<R, true, false>(S, a, si.x, io, x0, y0, y1);
+            else ok = sweep_item<R, false, false>(S, a, si.x, io, x0, y0, y1);
         }
         if (!ok) return;   // uniform: every thread saw the same __syncthreads_or
-        it = S.next;       // written before the item's barriers
+        if (a.stages > 1) {
+            // publish: every thread's stores of this item, then its flag
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                atomicExch(a.done + (size_t)S.stage * a.nitems + S.item, 1);
+            }
+        }
     }
 }
 

@@ -108,6 +108,7 @@ SIGNATURES = [
     ("eulbfs_load", ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_ulonglong, ct.c_longlong]),
     ("eulbfs_diagnostics", ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(Diag)]),
     ("eulbfs_launches_per_step", ct.c_int, [ct.c_void_p]),
+    ("eulbfs_set_whole_step", ct.c_int, [ct.c_void_p, ct.c_int]),
     ("eulbfs_use_graphs", ct.c_int, [ct.c_void_p, ct.c_int]),
     ("eulbfs_autotune", ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_float)]),
     ("eulbfs_set_tile", ct.c_int, [ct.c_void_p, ct.c_int]),
@@ -297,6 +298,10 @@ class Solver:
 
     def launches_per_step(self) -> int:
         return lib().eulbfs_launches_per_step(self._h)
+
+    def set_whole_step(self, on: bool = True):
+        """One kernel launch per time step (default) or one per Runge-Kutta stage."""
+        _check(lib().eulbfs_set_whole_step(self._h, 1 if on else 0))
 
     # -- outputs
     def fields(self, slot: int = 0, which=("H", "T", "Fl", "C", "p", "u", "v")) -> dict:

@@ -1,0 +1,127 @@
+"""One launch per time step (eulbfs_set_whole_step, the default) against one
+launch per Runge-Kutta stage.
+
+In a whole-step launch the work items of stage 1, 2 and 3 run in one grid;
+an item starts once the items of the previous stage whose output it reads
+are done (its strip and the strips beside it, its rows and 4 rows beyond,
+wrapped on periodic axes).  A missing neighbour in that list, or a wait that
+let an item read a neighbour's output too early, changes the result, so the
+two launch forms must agree bit for bit: on a mix of planar, axisymmetric,
+periodic-x, periodic-y, hysteresis-wall and general-streaming domains of
+ragged sizes, over several work-item heights, and on the 64-domain batch
+(more items than resident CTAs, so stages overlap).
+"""
+import numpy as np
+import pytest
+
+from paper_2507_03366_gb300 import eulbfs
+from paper_2507_03366_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("H", "T", "Fl", "C", "p", "u", "v")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2507_03366_gb300 import build
+    build.build()
+
+
+def _periodic_x(nx, ny):
+    rng = np.random.default_rng(nx + 7 * ny)
+    case = wl.droplet(max(nx, ny), theta_deg=70.0, St=0.25, Tw=-0.6).crop(nx, ny)
+    case.bc = wl.BC(wl.PER, wl.PER, wl.Side(wl.DIRICHLET_T, wl.NOSLIP, wl.WETTING, Tw=-0.6, theta_deg=70.0),
+                    wl.Side(wl.ADIABATIC, wl.OUTLET, wl.NOFLUX))
+    y = np.arange(ny) + 0.5
+    case.init["C"] = np.ascontiguousarray(np.broadcast_to((0.5 * (1 + np.tanh(2 * (ny / 2 - y) / 4.0)))[:, None],
+                                                          (ny, nx)))
+    case.init["T"] = case.init["T"] + 0.05 * rng.standard_normal((ny, nx))
+    case.init["u"] = 1e-3 * rng.standard_normal((ny, nx)) * case.init["C"]
+    return case
+
+
+def _periodic_y(nx, ny):
+    rng = np.random.default_rng(nx * 100 + ny)
+    case = wl.droplet(max(nx, ny), theta_deg=75.0, St=0.25, Tw=-0.6).crop(nx, ny)
+    case.bc = wl.BC(wl.Side(wl.DIRICHLET_T, wl.NOSLIP, wl.WETTING, Tw=-0.6, theta_deg=75.0),
+                    wl.Side(wl.ADIABATIC, wl.OUTLET, wl.NOFLUX), wl.PER, wl.PER)
+    x = np.arange(nx) + 0.5
+    case.init["C"] = np.ascontiguousarray(np.broadcast_to(0.5 * (1 + np.tanh(2 * (nx / 2 - x) / 4.0)), (ny, nx)))
+    case.init["T"] = case.init["T"] + 0.05 * rng.standard_normal((ny, nx))
+    return case
+
+
+def _mix():
+    gen = wl.droplet(70, theta_deg=95.0, St=0.3)
+    gen.dt_h, gen.dt_f, gen.dt_g = 0.3, 0.4, 0.3
+    return [
+        wl.droplet(96, theta_deg=82.0, St=0.3, axisymmetric=True, hysteresis=(100.0, 39.0), impact_speed=0.03),
+        _periodic_x(100, 48),
+        _periodic_y(37, 90),
+        wl.droplet(65, theta_deg=60.0, St=0.2),
+        gen,
+        wl.droplet(40, theta_deg=110.0, St=0.25, axisymmetric=True),
+        wl.film(128),
+    ]
+
+
+def _run(cases, precision, whole, steps, tile=0, graphs=0):
+    s = eulbfs.Solver(cases, precision=precision)
+    s.set_whole_step(whole)
+    if tile:
+        s.set_tile(tile)
+    if graphs:
+        s.use_graphs(graphs)
+    s.step(steps)
+    return s
+
+
+@pytest.mark.parametrize("precision", [eulbfs.FP32C, eulbfs.FP64])
+def test_whole_step_equals_stage_launches_on_a_mixed_batch(precision):
+    cases = _mix()
+    ref = _run(cases, precision, False, 30)
+    assert ref.launches_per_step() == 3
+    for tile in (8, 24, 64):
+        got = _run(cases, precision, True, 30, tile=tile, graphs=5 if tile == 24 else 0)
+        assert got.launches_per_step() == 1
+        for k in range(len(cases)):
+            a, b = got.fields(k), ref.fields(k)
+            for f in FIELDS:
+                assert np.array_equal(a[f], b[f]), (tile, k, f)
+        for k in range(len(cases)):
+            assert got.diag(k)["step"] == 30
+
+
+def test_whole_step_on_the_64_domain_batch():
+    """More items than resident CTAs: a stage's last items run while the next
+    stage's first ones do."""
+    cases = wl.static_droplet_batch(64, axisymmetric=True)
+    ref = _run(cases, eulbfs.FP32C, False, 6, tile=64)
+    got = _run(cases, eulbfs.FP32C, True, 6, tile=64)
+    for k in range(0, 64, 7):
+        a, b = got.fields(k), ref.fields(k)
+        for f in FIELDS:
+            assert np.array_equal(a[f], b[f]), (k, f)
+    # every domain, through its integrals
+    for k in range(64):
+        assert got.diag(k)["mass"] == ref.diag(k)["mass"], k
+
+
+def test_split_domains_launch_per_stage():
+    s = eulbfs.Solver([], precision=eulbfs.FP32C)
+    s.add_split(wl.film(256), 2)
+    assert s.launches_per_step() == 6
+    s.set_whole_step(False)
+    assert s.launches_per_step() == 6
+
+
+def test_whole_step_argument_checks():
+    s = eulbfs.Solver([wl.droplet(32)], precision=eulbfs.FP32C)
+    with pytest.raises(eulbfs.EulbfsError) as e:
+        eulbfs._check(eulbfs.lib().eulbfs_set_whole_step(s._h, 2))
+    assert e.value.code == eulbfs.EINVAL
+    s.set_whole_step(False)
+    assert s.launches_per_step() == 3
+    s.set_whole_step(True)
+    assert s.launches_per_step() == 1
