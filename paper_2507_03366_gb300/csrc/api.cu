@@ -168,7 +168,7 @@ size_t domain_bytes(long long n, int precision) {
 int eulbfs::set_error(int code, const char* msg) { return fail(code, msg); }
 
 constexpr int kMaxTune = 8;   // autotune candidates kept for eulbfs_autotune_report
-constexpr int kTailLevels = 2;   // halvings of the work list's last wave
+constexpr int kTailLevels = 2;   // halvings of the work list's last wave (launches per stage)
 
 struct eulbfs_solver {
     int precision = EULBFS_FP32C;
@@ -386,12 +386,19 @@ int rebuild(eulbfs_solver* s) {
     }
     const auto taller = [](const int4& a, const int4& b) { return a.w - a.z > b.w - b.z; };
     std::stable_sort(items.begin(), items.end(), taller);
-    // the end of the list in shorter items: kTailLevels times, the last wave
-    // (one item per resident CTA) is cut in half, so the launch ends on items
-    // 2^-kTailLevels as tall and the first CTAs to run out of work wait less
-    // for the last
+    // launches per stage (split domains exchange halos between stages, or
+    // eulbfs_set_whole_step(0)): the end of the list in shorter items --
+    // kTailLevels times, the last wave (one item per resident CTA) is cut in
+    // half, so each launch ends on items 2^-kTailLevels as tall and the first
+    // CTAs to run out of work wait less for the last.  A whole-step launch
+    // has no stage ends to shorten (the next stage's items fill them), and
+    // its one end gains less than the extra prologues cost.
+    bool linked = false;
+    for (const int2& l : s->links)
+        linked |= l.x < nd && l.y < nd && s->doms[l.x].active() && s->doms[l.y].active();
+    const int tail_levels = s->whole_step && !linked ? 0 : kTailLevels;
     const int resident = stage_blocks_per_sm(s->precision) * s->sms;
-    for (int level = 0; level < kTailLevels && (long long)items.size() > 2LL * resident; ++level) {
+    for (int level = 0; level < tail_levels && (long long)items.size() > 2LL * resident; ++level) {
         std::vector<int4> tail;
         for (size_t i = items.size() - resident; i < items.size(); ++i) {
             const int4 t = items[i];
