@@ -41,20 +41,20 @@ STAGES = 3
 BYTES_COMPULSORY = {1: 64, 0: 96}
 BYTES_STAGE_BY_STAGE = {1: 244, 0: 352}
 # Counters of the FP32C and FP64 stage kernels from ncu captures of the
-# 64-domain batch (6.80 M cells, work items of 64 rows, stages 0-2 of one
-# step, planar and axisymmetric), per cell and stage: FP32 (FP64)
-# operations with an FMA counted as 2, warp instructions issued, and DRAM
-# bytes per launch.  They belong to one version of the kernel's sources: the
+# 64-domain batch (6.80 M cells, work items of 96 rows, one whole-step
+# launch, planar and axisymmetric): per cell and stage, FP32 (FP64)
+# operations with an FMA counted as 2 and warp instructions issued; per
+# cell and step, DRAM bytes.  They belong to one version of the kernel's sources: the
 # SHA-256 of stage.cu + device_common.cuh + eulbfs_internal.h.  When the
 # sources change, the counters are reported as stale (null) until they are
 # captured again.
 KERNEL_SOURCES = ("stage.cu", "device_common.cuh", "eulbfs_internal.h")
 COUNTERS = {
-    "sources_sha256": "9951096500acc887bf85669c9f0cef19049ff316a44d25c0a2ea48dc0246cfbe",
-    "fp32_flops_per_cell_stage": {"rz": 947.8, "xy": 909.7},
-    "warp_inst_per_cell_stage": {"rz": 45.23, "xy": 43.87},
-    "dram_bytes_per_cell_step": {"rz": 244.9, "xy": 244.2},
-    "fp64_flops_per_cell_stage": {"rz": 1025.1, "xy": 949.8},
+    "sources_sha256": "95b0a165d09874cc62b9dd520fbcc70280cb436ed30e449471f7ed1a9ba949c4",
+    "fp32_flops_per_cell_stage": {"rz": 944.0, "xy": 906.5},
+    "warp_inst_per_cell_stage": {"rz": 44.94, "xy": 43.65},
+    "dram_bytes_per_cell_step": {"rz": 312.1, "xy": 305.6},
+    "fp64_flops_per_cell_stage": {"rz": 1014.8, "xy": 942.3},
 }
 # Streaming steps (dt_h, dt_f, dt_g) of the general-face-path leg.
 GEN_STEPS = (0.3, 0.4, 0.3)
