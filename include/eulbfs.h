@@ -362,7 +362,11 @@ int eulbfs_autotune(eulbfs_solver* s, int steps_per_candidate, int* best_rows, f
  * flight) and the kernel stops; eulbfs_sync then returns ETIMEOUT and the
  * CUDA context stays usable.  on = 0 (the default) restores normal waits.
  * Only domains whose state buffers get tensor maps (nx a multiple of 4 in
- * FP32C) and interior work items wait on tiles.  Errors: EINVAL. */
+ * FP32C) and interior work items wait on tiles.  With on = 2 the tiles are
+ * normal but no work item of a whole-step launch (eulbfs_set_whole_step)
+ * marks itself done, so every item of stages 2 and 3 waits out its bound
+ * for the items it reads and the kernel stops with the same ETIMEOUT (both
+ * precisions).  Errors: EINVAL. */
 int eulbfs_set_tile_wait_probe(eulbfs_solver* s, int on);
 
 /* The candidates the last eulbfs_autotune of this solver timed: up to `cap`

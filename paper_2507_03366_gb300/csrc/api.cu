@@ -212,7 +212,8 @@ struct eulbfs_solver {
     int tune_n = 0;
     int tune_rows[kMaxTune] = {};
     float tune_ms[kMaxTune] = {};
-    unsigned tile_probe = 0;       // eulbfs_set_tile_wait_probe
+    unsigned tile_probe = 0;       // eulbfs_set_tile_wait_probe(1)
+    int dep_probe = 0;             // eulbfs_set_tile_wait_probe(2)
     // split domains: (lower slab, upper slab) pairs whose halo rows are
     // exchanged after every stage; the active ones on the device
     std::vector<int2> links;
@@ -472,6 +473,7 @@ int launch_step_direct(eulbfs_solver* s) {
     a.consts = s->d_consts;
     a.tmaps = s->d_tmaps;
     a.tile_probe = s->tile_probe;
+    a.dep_probe = s->dep_probe;
     a.items = s->d_items;
     a.nitems = s->nitems;
     a.flag = s->d_flag;
@@ -818,8 +820,9 @@ int eulbfs_autotune_report(const eulbfs_solver* s, int* rows, float* ms_per_step
 }
 
 int eulbfs_set_tile_wait_probe(eulbfs_solver* s, int on) {
-    if (!s || (on != 0 && on != 1)) return fail(EULBFS_EINVAL, "null solver or on not 0/1");
-    s->tile_probe = on ? 16u : 0u;
+    if (!s || on < 0 || on > 2) return fail(EULBFS_EINVAL, "null solver or on not 0, 1 or 2");
+    s->tile_probe = on == 1 ? 16u : 0u;
+    s->dep_probe = on == 2 ? 1 : 0;
     drop_graph(s);
     return EULBFS_OK;
 }

@@ -183,6 +183,7 @@ struct StageLaunch {
     int* done;               // [3][nitems], zeroed before each step
     int* flag;               // bit 0: non-finite state seen; bit 1: a bounded wait (tile or neighbour) gave up
     unsigned tile_probe;     // bytes each tile barrier expects beyond its copy (0; > 0 only to test the bounded waits)
+    int dep_probe;           // 1: items never mark themselves done (only to test the bounded neighbour waits)
 };
 
 // Launch one Runge-Kutta stage (stages == 1) or a whole step (stages == 3)

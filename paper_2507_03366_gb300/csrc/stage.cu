@@ -1186,7 +1186,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) stage_kernel(Stage
         if (a.stages > 1) {
             // publish: every thread's stores of this item, then its flag
             __syncthreads();
-            if (tid == 0) {
+            if (tid == 0 && !a.dep_probe) {
                 __threadfence();
                 atomicExch(a.done + (size_t)S.stage * a.nitems + S.item, 1);
             }

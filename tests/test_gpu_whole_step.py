@@ -125,3 +125,30 @@ def test_whole_step_argument_checks():
     assert s.launches_per_step() == 3
     s.set_whole_step(True)
     assert s.launches_per_step() == 1
+
+
+@pytest.mark.parametrize("precision", [eulbfs.FP32C, eulbfs.FP64])
+def test_bounded_neighbour_wait_reports_timeout_and_context_survives(precision):
+    """Failure detection without a fault: with probe 2 no work item marks
+    itself done, so every stage-2 item waits out its bound (about a second of
+    SM clocks) for the items it reads, the kernel stops and the host reads
+    ETIMEOUT.  The context stays usable: two fresh solvers then agree bit for
+    bit."""
+    import time
+    case = wl.droplet(96, theta_deg=90.0, St=0.3)
+    s = eulbfs.Solver([case], precision=precision)
+    with pytest.raises(eulbfs.EulbfsError) as e:
+        eulbfs._check(eulbfs.lib().eulbfs_set_tile_wait_probe(s._h, 3))
+    assert e.value.code == eulbfs.EINVAL
+    eulbfs._check(eulbfs.lib().eulbfs_set_tile_wait_probe(s._h, 2))
+    t0 = time.perf_counter()
+    s.step(1)
+    with pytest.raises(eulbfs.EulbfsError) as e:
+        s.sync()
+    assert e.value.code == eulbfs.ETIMEOUT
+    assert time.perf_counter() - t0 < 60.0
+    s.close()
+    a = _run([case], precision, True, 5)
+    b = _run([case], precision, False, 5)
+    for f in FIELDS:
+        assert np.array_equal(a.fields()[f], b.fields()[f]), f
