@@ -22,16 +22,24 @@ template <> struct Prec<float> { static constexpr int NP = 7; };
 template <class R>
 struct SV { R Hh, Hl, p, mx, my, Ch, Cl; };
 
+// Loads of data that other CTAs write during the same launch (a stage's
+// output, read by the next stage of a whole-step launch; F_s and dF_s/dt)
+// are cached in L2 only: an SM's L1 is not kept coherent with other SMs'
+// stores, and a line it cached earlier in the launch could span cells that
+// were written after it was read.
+template <class T>
+__device__ __forceinline__ T ld_l2(const T* p) { return __ldcg(p); }
+
 __device__ __forceinline__ SV<double> load_state(const double* b, long long P, long long c) {
     SV<double> s;
-    s.Hh = b[c]; s.Hl = 0.0; s.p = b[P + c]; s.mx = b[2 * P + c]; s.my = b[3 * P + c];
-    s.Ch = b[4 * P + c]; s.Cl = 0.0;
+    s.Hh = ld_l2(b + c); s.Hl = 0.0; s.p = ld_l2(b + P + c); s.mx = ld_l2(b + 2 * P + c);
+    s.my = ld_l2(b + 3 * P + c); s.Ch = ld_l2(b + 4 * P + c); s.Cl = 0.0;
     return s;
 }
 __device__ __forceinline__ SV<float> load_state(const float* b, long long P, long long c) {
     SV<float> s;
-    s.Hh = b[c]; s.Hl = b[P + c]; s.p = b[2 * P + c]; s.mx = b[3 * P + c]; s.my = b[4 * P + c];
-    s.Ch = b[5 * P + c]; s.Cl = b[6 * P + c];
+    s.Hh = ld_l2(b + c); s.Hl = ld_l2(b + P + c); s.p = ld_l2(b + 2 * P + c); s.mx = ld_l2(b + 3 * P + c);
+    s.my = ld_l2(b + 4 * P + c); s.Ch = ld_l2(b + 5 * P + c); s.Cl = ld_l2(b + 6 * P + c);
     return s;
 }
 __device__ __forceinline__ void store_state(double* b, long long P, long long c, const SV<double>& s) {
@@ -156,8 +164,10 @@ template <class R>
 struct Prim { R T, Fl, cp, rho, lam, mu, p, u, v, C; };
 
 // Phase field C = C_hi + C_lo of cell c of a state buffer.
-__device__ __forceinline__ double load_C(const double* b, long long P, long long c) { return b[4 * P + c]; }
-__device__ __forceinline__ float load_C(const float* b, long long P, long long c) { return b[5 * P + c] + b[6 * P + c]; }
+__device__ __forceinline__ double load_C(const double* b, long long P, long long c) { return ld_l2(b + 4 * P + c); }
+__device__ __forceinline__ float load_C(const float* b, long long P, long long c) {
+    return ld_l2(b + 5 * P + c) + ld_l2(b + 6 * P + c);
+}
 
 // Wetting coefficient 4 cos(theta) / xi of the wall position t of `side`
 // (the row of an x side, the column of a y side; clamped into the domain or

@@ -979,11 +979,11 @@ __device__ __forceinline__ void cell_update(Smem<R>& S, int stage, int x0, int r
     if (stage == 0) {   // reading R14: lagged dF_s/dt, fixed over the step
         R* Fsp = reinterpret_cast<R*>(K.Fsp);
         const R Fs = R(1) - Fl;
-        dfs = (Fs - Fsp[c]) * cc.w;
+        dfs = (Fs - ld_l2(Fsp + c)) * cc.w;
         reinterpret_cast<R*>(K.dFs)[c] = dfs;
         Fsp[c] = Fs;
     } else {
-        dfs = reinterpret_cast<const R*>(K.dFs)[c];
+        dfs = ld_l2(reinterpret_cast<const R*>(K.dFs) + c);
     }
     const R cs2 = R(1.0 / 3.0);
     const R D = solid_gate(K, C) * dfs;
