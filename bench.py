@@ -50,10 +50,10 @@ BYTES_STAGE_BY_STAGE = {1: 244, 0: 352}
 # captured again.
 KERNEL_SOURCES = ("stage.cu", "device_common.cuh", "eulbfs_internal.h")
 COUNTERS = {
-    "sources_sha256": "b396da078b74f8a6568436fbb63a4646da1dbfacc7ec838e21816106ac6f81e3",
+    "sources_sha256": "653fa1bbcbb75dddfc6b1d0cd98e8832cb443131621d6516b9ea4b52793d41b1",
     "fp32_flops_per_cell_stage": {"rz": 944.0, "xy": 906.5},
-    "warp_inst_per_cell_stage": {"rz": 44.94, "xy": 43.65},
-    "dram_bytes_per_cell_step": {"rz": 314.4, "xy": 303.2},
+    "warp_inst_per_cell_stage": {"rz": 45.06, "xy": 43.73},
+    "dram_bytes_per_cell_step": {"rz": 311.7, "xy": 308.3},
     "fp64_flops_per_cell_stage": {"rz": 1014.8, "xy": 942.3},
 }
 # Streaming steps (dt_h, dt_f, dt_g) of the general-face-path leg.
