@@ -285,17 +285,24 @@ int eulbfs_load(eulbfs_solver* s, int slot, const void* buf, unsigned long long 
 int eulbfs_diagnostics(eulbfs_solver* s, int slot, eulbfs_diag* d);
 
 /* Number of kernels the solver launches per time step of the current batch:
- * one whole-step launch (eulbfs_set_whole_step); three stage launches with
- * it off; and while a split domain's slabs are active, three stage launches
+ * one whole-step launch (eulbfs_set_whole_step; an eulbfs_step of several
+ * steps runs up to 16 of them in one launch); three stage launches with it
+ * off; and while a split domain's slabs are active, three stage launches
  * with a halo copy after each. */
 int eulbfs_launches_per_step(const eulbfs_solver* s);
 
-/* One launch per time step (on = 1, the default) or one per Runge-Kutta
+/* Kernel launches of the time-stepping path (stage kernels and halo copies,
+ * including those replayed from captured graphs) since the solver was
+ * created; 0 for a null solver. */
+unsigned long long eulbfs_launch_count(const eulbfs_solver* s);
+
+/* Whole-step launches (on = 1, the default) or one launch per Runge-Kutta
  * stage (on = 0).  A whole-step launch runs the work items of stage 1, then
- * stage 2, then stage 3 (Eq. 58), each item as soon as the items of the
- * previous stage whose output it reads (its strip and the strips beside it,
- * its rows and 4 rows beyond) are done, so one stage's last items overlap
- * the next stage's first.  Batches with split domains always launch per
+ * stage 2, then stage 3 (Eq. 58) of one time step, or of up to 16 steps in
+ * sequence (an eulbfs_step of several steps, up to the next domain's step
+ * limit), each item as soon as the items of the previous stage whose output
+ * it reads (its strip and the strips beside it, its rows and 4 rows beyond)
+ * are done, so one stage's last items overlap the next stage's first.  Batches with split domains always launch per
  * stage (their halo copies run between stages).  Results are the same bit
  * for bit.  A wait for a neighbour's item is bounded (about a second) and
  * reports EULBFS_ETIMEOUT like a tile wait.  Errors: EINVAL. */

@@ -169,6 +169,7 @@ int eulbfs::set_error(int code, const char* msg) { return fail(code, msg); }
 
 constexpr int kMaxTune = 8;   // autotune candidates kept for eulbfs_autotune_report
 constexpr int kTailLevels = 2;   // halvings of the work list's last wave (launches per stage)
+constexpr int kMaxLaunchSteps = 16;   // time steps in one whole-step launch at most
 
 struct eulbfs_solver {
     int precision = EULBFS_FP32C;
@@ -189,13 +190,15 @@ struct eulbfs_solver {
     int* d_flag = nullptr;
     // item counters ([0..3]) and the whole-step launch's done flags ([3][nitems])
     int* d_sched = nullptr;
-    int sched_cap = 0;
+    size_t sched_cap = 0;
     // whole-step launches: each item's neighbourhood (CSR: offsets, then indices)
     int* d_deps = nullptr;
     int deps_cap = 0;
     int ndeps = 0;
     bool whole_step = true;        // eulbfs_set_whole_step: one launch per step where possible
     bool fused = false;            // this batch runs whole-step launches
+    unsigned long long launches = 0;        // kernel launches run so far (eulbfs_launch_count)
+    unsigned long long graph_launches = 0;  // kernel launches in one replay of the captured graph
     int* h_flag = nullptr;
     int* h_flags = nullptr;        // pinned, one per slot: per-domain non-finite flags
     int h_flags_cap = 0;
@@ -439,7 +442,7 @@ int rebuild(eulbfs_solver* s) {
     if (s->nlinks) CK(cudaMemcpyAsync(s->d_links, act.data(), sizeof(int2) * s->nlinks, cudaMemcpyHostToDevice, s->stream), "upload links");
     // counters and done flags; the neighbourhoods of a whole-step launch
     // (split domains exchange halos between stages: one launch per stage)
-    const int sched = 4 + 3 * s->nitems;
+    const size_t sched = 4 + (size_t)3 * kMaxLaunchSteps * s->nitems;
     if (sched > s->sched_cap) {
         if (s->d_sched) cudaFree(s->d_sched);
         s->d_sched = nullptr;
@@ -468,7 +471,10 @@ int rebuild(eulbfs_solver* s) {
     return EULBFS_OK;
 }
 
-int launch_step_direct(eulbfs_solver* s) {
+// k time steps on the solver's stream: whole-step launches of up to
+// kMaxLaunchSteps steps each, or three stage launches per step (with the
+// split domains' halo copies after each).
+int launch_steps_direct(eulbfs_solver* s, long long k) {
     StageLaunch a;
     a.consts = s->d_consts;
     a.tmaps = s->d_tmaps;
@@ -482,27 +488,37 @@ int launch_step_direct(eulbfs_solver* s) {
     a.dep_off = s->d_deps;
     a.dep_idx = s->d_deps + (s->nitems + 1);
     a.stage = 0;
-    // counters (and done flags) start at zero every step: an aborted step cannot leave one behind
-    const size_t zero = sizeof(int) * (s->fused ? 4 + 3 * (size_t)s->nitems : 4);
-    if (cudaMemsetAsync(s->d_sched, 0, zero, s->stream) != cudaSuccess) return cuda_fail(cudaGetLastError(), "work counters");
-    if (s->fused) {
-        a.stages = 3;
-        nvtxRangePushA("eulbfs step");
-        const cudaError_t e = launch_stage(s->precision, a, s->grid, s->stream);
-        nvtxRangePop();
-        return e == cudaSuccess ? EULBFS_OK : cuda_fail(e, "stage kernel launch");
-    }
-    a.stages = 1;
     static const char* const kStageRange[3] = {"eulbfs RK stage 1", "eulbfs RK stage 2", "eulbfs RK stage 3"};
-    for (int st = 0; st < 3; ++st) {
-        a.stage = st;
-        nvtxRangePushA(kStageRange[st]);
-        cudaError_t e = launch_stage(s->precision, a, s->grid, s->stream);
-        // split domains: the stage's output halos from the neighbouring slabs
-        if (e == cudaSuccess && s->nlinks)
-            e = launch_halo(s->precision, s->d_consts, s->d_links, s->nlinks, s->link_nx, st == 2 ? 0 : st + 1, s->stream);
-        nvtxRangePop();
-        if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
+    while (k > 0) {
+        // counters and done flags start at zero every launch: an aborted launch cannot leave one behind
+        const int steps = s->fused ? (int)std::min<long long>(k, kMaxLaunchSteps) : 1;
+        const size_t zero = sizeof(int) * (s->fused ? 4 + 3 * (size_t)steps * s->nitems : 4);
+        if (cudaMemsetAsync(s->d_sched, 0, zero, s->stream) != cudaSuccess) return cuda_fail(cudaGetLastError(), "work counters");
+        if (s->fused) {
+            a.stages = 3 * steps;
+            nvtxRangePushA("eulbfs steps");
+            const cudaError_t e = launch_stage(s->precision, a, s->grid, s->stream);
+            nvtxRangePop();
+            if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
+            ++s->launches;
+        } else {
+            a.stages = 1;
+            for (int st = 0; st < 3; ++st) {
+                a.stage = st;
+                nvtxRangePushA(kStageRange[st]);
+                cudaError_t e = launch_stage(s->precision, a, s->grid, s->stream);
+                ++s->launches;
+                // split domains: the stage's output halos from the neighbouring slabs
+                if (e == cudaSuccess && s->nlinks) {
+                    e = launch_halo(s->precision, s->d_consts, s->d_links, s->nlinks, s->link_nx, st == 2 ? 0 : st + 1,
+                                    s->stream);
+                    ++s->launches;
+                }
+                nvtxRangePop();
+                if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
+            }
+        }
+        k -= steps;
     }
     return EULBFS_OK;
 }
@@ -513,8 +529,11 @@ int capture_graph(eulbfs_solver* s) {
         cudaGetLastError();
         return EULBFS_ECUDA;
     }
-    int rc = EULBFS_OK;
-    for (int k = 0; k < s->graph_steps && rc == EULBFS_OK; ++k) rc = launch_step_direct(s);
+    // the capture records launches without running them: count them once per replay
+    const unsigned long long before = s->launches;
+    int rc = launch_steps_direct(s, s->graph_steps);
+    s->graph_launches = s->launches - before;
+    s->launches = before;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s->stream, &g);
     if (rc != EULBFS_OK || e != cudaSuccess || !g) {
@@ -845,6 +864,8 @@ int eulbfs_launches_per_step(const eulbfs_solver* s) {
     return s->whole_step && any ? 1 : 3;
 }
 
+unsigned long long eulbfs_launch_count(const eulbfs_solver* s) { return s ? s->launches : 0; }
+
 int eulbfs_set_whole_step(eulbfs_solver* s, int on) {
     if (!s || (on != 0 && on != 1)) return fail(EULBFS_EINVAL, "null solver or on not 0/1");
     if (s->whole_step != (on == 1)) {
@@ -897,8 +918,10 @@ int eulbfs_step(eulbfs_solver* s, long long n) {
         }
         if (s->nitems == 0) break;
         if (s->halo_stale) {   // W^n written by creation, set_state or load: its halos first
-            if (s->nlinks)
+            if (s->nlinks) {
                 CK(launch_halo(s->precision, s->d_consts, s->d_links, s->nlinks, s->link_nx, 0, s->stream), "halo rows");
+                ++s->launches;
+            }
             s->halo_stale = false;
         }
         long long k = n;
@@ -912,11 +935,12 @@ int eulbfs_step(eulbfs_solver* s, long long n) {
                 const cudaError_t ge = cudaGraphLaunch(s->graph, s->stream);
                 nvtxRangePop();
                 CK(ge, "graph launch");
+                s->launches += s->graph_launches;
                 left -= s->graph_steps;
             }
         }
-        for (; left > 0; --left) {
-            int rc = launch_step_direct(s);
+        if (left > 0) {
+            int rc = launch_steps_direct(s, left);
             if (rc) return rc;
         }
         for (Dom& d : s->doms)

@@ -173,20 +173,20 @@ struct StageLaunch {
     const int4* items;       // (domain, strip, y0, y1), tallest first
     int nitems;
     int stage;               // the stage of a one-stage launch: 0, 1, 2
-    int stages;              // 1: stage `stage` alone; 3: a whole time step (items of stage 0, then 1, then 2)
+    int stages;              // 1: stage `stage` alone; 3 k: k whole time steps (items of stage 0, 1, 2 of the first step, then of the next)
     int* work;               // item counters (per stage; [0] for a whole-step launch), zeroed before each step
     // whole-step launches: item i of stage s reads the output of the stage
     // s - 1 items dep_idx[dep_off[i] .. dep_off[i + 1]) (its neighbourhood),
     // and waits until done[(s - 1) * nitems + j] is set for each of them
     const int* dep_off;
     const int* dep_idx;
-    int* done;               // [3][nitems], zeroed before each step
+    int* done;               // [stages][nitems], zeroed before each launch
     int* flag;               // bit 0: non-finite state seen; bit 1: a bounded wait (tile or neighbour) gave up
     unsigned tile_probe;     // bytes each tile barrier expects beyond its copy (0; > 0 only to test the bounded waits)
     int dep_probe;           // 1: items never mark themselves done (only to test the bounded neighbour waits)
 };
 
-// Launch one Runge-Kutta stage (stages == 1) or a whole step (stages == 3)
+// Launch one Runge-Kutta stage (stages == 1) or k whole steps (stages == 3 k)
 // over every work item of the batch.
 cudaError_t launch_stage(int precision, const StageLaunch& a, int grid, cudaStream_t s);
 // Resident CTAs per SM of the stage kernel (for sizing the persistent grid).

@@ -139,7 +139,8 @@ __device__ __forceinline__ void tile_fetch(Smem<R>& S, const StageLaunch& a, int
     if (threadIdx.x == 0) tile_fetch_from(S, a, stage, S.cur_domain, S.K.hlo, x0, r0);
 }
 
-// Position g of a launch's item sequence: its stage and work item.
+// Position g of a launch's item sequence: its stage (counted over the
+// launch: 3 k + s for Runge-Kutta stage s of the launch's step k) and work item.
 __device__ __forceinline__ int2 stage_item(const StageLaunch& a, int g) {
     if (a.stages == 1) return make_int2(a.stage, g);
     const int st = g / a.nitems;
@@ -194,7 +195,7 @@ __device__ __forceinline__ void tile_prefetch_next(Smem<R>& S, const StageLaunch
             if (lane == 0) {
                 // the rows were written by other CTAs through the generic proxy
                 asm volatile("fence.proxy.async.global;" ::: "memory");
-                tile_fetch_from(S, a, si.x, item.x, Kn.hlo, x0, y0 - kHalo);
+                tile_fetch_from(S, a, si.x % 3, item.x, Kn.hlo, x0, y0 - kHalo);
             }
             pre = 1;
         }
@@ -1138,8 +1139,9 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) stage_kernel(Stage
     // Every item is claimed from the launch's counter, one item ahead (the
     // tile prefetch of the next item's prologue needs to know it).  In a
     // whole-step launch the items of stage 1 follow all of stage 0 and those
-    // of stage 2 all of stage 1, and an item waits for the items of the
-    // previous stage it reads.  Only running CTAs hold items, and every item
+    // of stage 2 all of stage 1 (then stage 0 of the next step, when the
+    // launch runs several), and an item waits for the items of the previous
+    // stage it reads.  Only running CTAs hold items, and every item
     // waits only for items claimed before it, so the earliest unfinished
     // item can always proceed.
     int* const counter = a.work + (a.stages == 1 ? a.stage : 0);
@@ -1176,11 +1178,11 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) stage_kernel(Stage
         const int y0 = item.z, y1 = item.w;
         bool ok;
         if (S.K.gen) {   // some streaming step differs from 1/2 (reading R26)
-            if (S.K.axi) ok = sweep_item<R, true, true>(S, a, si.x, io, x0, y0, y1);
-            else ok = sweep_item<R, false, true>(S, a, si.x, io, x0, y0, y1);
+            if (S.K.axi) ok = sweep_item<R, true, true>(S, a, si.x % 3, io, x0, y0, y1);
+            else ok = sweep_item<R, false, true>(S, a, si.x % 3, io, x0, y0, y1);
         } else {
-            if (S.K.axi) ok = sweep_item<R, true, false>(S, a, si.x, io, x0, y0, y1);
-            else ok = sweep_item<R, false, false>(S, a, si.x, io, x0, y0, y1);
+            if (S.K.axi) ok = sweep_item<R, true, false>(S, a, si.x % 3, io, x0, y0, y1);
+            else ok = sweep_item<R, false, false>(S, a, si.x % 3, io, x0, y0, y1);
         }
         if (!ok) return;   // uniform: every thread saw the same __syncthreads_or
         if (a.stages > 1) {

@@ -109,6 +109,7 @@ SIGNATURES = [
     ("eulbfs_diagnostics", ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(Diag)]),
     ("eulbfs_launches_per_step", ct.c_int, [ct.c_void_p]),
     ("eulbfs_set_whole_step", ct.c_int, [ct.c_void_p, ct.c_int]),
+    ("eulbfs_launch_count", ct.c_ulonglong, [ct.c_void_p]),
     ("eulbfs_use_graphs", ct.c_int, [ct.c_void_p, ct.c_int]),
     ("eulbfs_autotune", ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_float)]),
     ("eulbfs_set_tile", ct.c_int, [ct.c_void_p, ct.c_int]),
@@ -298,6 +299,10 @@ class Solver:
 
     def launches_per_step(self) -> int:
         return lib().eulbfs_launches_per_step(self._h)
+
+    def launch_count(self) -> int:
+        """Kernel launches of the time-stepping path since creation."""
+        return int(lib().eulbfs_launch_count(self._h))
 
     def set_whole_step(self, on: bool = True):
         """One kernel launch per time step (default) or one per Runge-Kutta stage."""

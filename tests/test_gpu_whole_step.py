@@ -152,3 +152,33 @@ def test_bounded_neighbour_wait_reports_timeout_and_context_survives(precision):
     b = _run([case], precision, False, 5)
     for f in FIELDS:
         assert np.array_equal(a.fields()[f], b.fields()[f]), f
+
+
+def test_several_steps_per_launch_equal_single_steps():
+    """An eulbfs_step of many steps runs up to 16 whole steps in one launch
+    (stage 1 of a step waits for stage 3 of the step before, item by item);
+    a domain's step limit inside that span cuts the launch there."""
+    cases = _mix()[:4]
+    a = eulbfs.Solver(cases, precision=eulbfs.FP32C)
+    n0 = a.launch_count()
+    a.step(37)                                   # launches of 16, 16 and 5 steps
+    assert a.launch_count() - n0 == 3
+    b = eulbfs.Solver(cases, precision=eulbfs.FP32C)
+    for _ in range(37):
+        b.step(1)
+    assert b.launch_count() == 37
+    for k in range(len(cases)):
+        for f in FIELDS:
+            assert np.array_equal(a.fields(k)[f], b.fields(k)[f]), (k, f)
+    # a step limit at 7: the first launch stops there, the rest carry on
+    c = eulbfs.Solver([cases[0]], precision=eulbfs.FP32C)
+    slot = c.add(cases[1], max_steps=7)
+    c.step(20)
+    assert c.progress(slot)[0] == 7 and c.progress(0)[0] == 20
+    alone = eulbfs.Solver([cases[1]], precision=eulbfs.FP32C)
+    alone.step(7)
+    ref0 = eulbfs.Solver([cases[0]], precision=eulbfs.FP32C)
+    ref0.step(20)
+    for f in FIELDS:
+        assert np.array_equal(c.fields(slot)[f], alone.fields()[f]), f
+        assert np.array_equal(c.fields(0)[f], ref0.fields()[f]), f
