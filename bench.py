@@ -41,8 +41,8 @@ STAGES = 3
 BYTES_COMPULSORY = {1: 64, 0: 96}
 BYTES_STAGE_BY_STAGE = {1: 244, 0: 352}
 # Counters of the FP32C and FP64 stage kernels from ncu captures of the
-# 64-domain batch (6.80 M cells, work items of 96 rows, one whole-step
-# launch, planar and axisymmetric): per cell and stage, FP32 (FP64)
+# 64-domain batch (6.80 M cells, work items of 128 rows, a 16-step launch
+# (FP64: 2 steps), planar and axisymmetric): per cell and stage, FP32 (FP64)
 # operations with an FMA counted as 2 and warp instructions issued; per
 # cell and step, DRAM bytes.  They belong to one version of the kernel's sources: the
 # SHA-256 of stage.cu + device_common.cuh + eulbfs_internal.h.  When the
@@ -50,11 +50,11 @@ BYTES_STAGE_BY_STAGE = {1: 244, 0: 352}
 # captured again.
 KERNEL_SOURCES = ("stage.cu", "device_common.cuh", "eulbfs_internal.h")
 COUNTERS = {
-    "sources_sha256": "653fa1bbcbb75dddfc6b1d0cd98e8832cb443131621d6516b9ea4b52793d41b1",
-    "fp32_flops_per_cell_stage": {"rz": 944.0, "xy": 906.5},
-    "warp_inst_per_cell_stage": {"rz": 45.06, "xy": 43.73},
-    "dram_bytes_per_cell_step": {"rz": 311.7, "xy": 308.3},
-    "fp64_flops_per_cell_stage": {"rz": 1014.8, "xy": 942.3},
+    "sources_sha256": "cbface8b97d14d2489ffbb3e171fe71d595a2fff85d003d3b12838e4224168c8",
+    "fp32_flops_per_cell_stage": {"rz": 942.3, "xy": 905.0},
+    "warp_inst_per_cell_stage": {"rz": 44.84, "xy": 43.53},
+    "dram_bytes_per_cell_step": {"rz": 350.6, "xy": 345.1},
+    "fp64_flops_per_cell_stage": {"rz": 1011.7, "xy": 940.4},
 }
 # Streaming steps (dt_h, dt_f, dt_g) of the general-face-path leg.
 GEN_STEPS = (0.3, 0.4, 0.3)
