@@ -353,7 +353,7 @@ int eulbfs_diagnostics_noalloc(int precision, const void* state, int nx, int ny,
                                const eulbfs_props* props, double* out, void* stream);
 
 /* Pick the work-item height of the current batch by timing each candidate
- * (24, 32, 40, 48, 64, 96, 128, 256 rows) over steps_per_candidate steps on
+ * (32, 48, 64, 96, 128, 160, 192, 256 rows) over steps_per_candidate steps on
  * the solver's stream, in two rounds, and keeping the candidate with the
  * fastest of its two timings (*best_ms_per_step).  The timed steps are real
  * steps of every active domain (results do not depend on the height), so the

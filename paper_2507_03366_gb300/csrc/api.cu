@@ -775,7 +775,7 @@ int eulbfs_set_tile(eulbfs_solver* s, int rows) {
 int eulbfs_autotune(eulbfs_solver* s, int steps_per_candidate, int* best_rows, float* best_ms_per_step) {
     if (!s) return fail(EULBFS_EINVAL, "null solver");
     if (steps_per_candidate < 1) return fail(EULBFS_EINVAL, "steps_per_candidate must be >= 1");
-    static const int kCandidates[] = {24, 32, 40, 48, 64, 96, 128, 256};
+    static const int kCandidates[] = {32, 48, 64, 96, 128, 160, 192, 256};
     static_assert(sizeof(kCandidates) / sizeof(kCandidates[0]) <= kMaxTune, "report arrays");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0), "event");

@@ -267,8 +267,8 @@ def test_autotune_picks_a_candidate_and_steps_as_documented():
     cases = wl.static_droplet_batch(3, sides=(40, 72), axisymmetric=True)
     s = eulbfs.Solver(cases, precision=eulbfs.FP32C)
     rows, ms = s.autotune(2)
-    assert rows in (24, 32, 40, 48, 64, 96, 128, 256) and ms > 0
-    assert sorted(s.autotune_report()) == [24, 32, 40, 48, 64, 96, 128, 256]
+    assert rows in (32, 48, 64, 96, 128, 160, 192, 256) and ms > 0
+    assert sorted(s.autotune_report()) == [32, 48, 64, 96, 128, 160, 192, 256]
     steps = 2 * 8 * (2 + 1)               # two rounds over eight heights, each 1 + 2 steps
     assert s.diag(0)["step"] == steps
     ref = eulbfs.Solver(cases, precision=eulbfs.FP32C)
